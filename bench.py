@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free Stokes operator (RT_k x DGQ_k, Algorithm 1).
+
+Default workload: one FP64 apply y = A x on the unit cube with 64^3 cells at
+k = 3 (67,305,472 DoF), the operator throughput sweep's largest k = 3 case.
+A step is one whole apply (velocity-row kernel + pressure-row kernel) over the
+seeded input vector, which stays resident in HBM (x and y are 539 MB each,
+larger than the 129 MB L2, so no flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one independent replica per GPU (the path has no
+data exchange between problems: weak scaling); rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle (the assembled CSR matrix of the
+paper's bilinear form) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Stokes apply GDoF/s (% HBM roofline); MG solve s/MDoF to 1e-8, mixed vs FP64"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# FP64 ALU peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def velocity_flops_per_dof(k: int) -> float:
+    """Algorithmic flops of the velocity rows per velocity DoF (Kronecker form, cell-local).
+
+    Per new node: the two 1D interior-penalty operators (block tridiagonal,
+    3 (k+1) FMA each) and 3 scalings; per cell line: KC and MC contractions
+    (2 (k+2)^2 FMA) and D^T p ((k+1)(k+2) FMA) plus k+1 scalings.
+    """
+    nd, nc = k + 1, k + 2
+    per_cell = nd * (6 * nd + 3) + 2 * nc * nc + nd * nc + nd
+    return 2.0 * per_cell / nd
+
+
+def pressure_flops_per_dof(k: int) -> float:
+    return 2.0 * (3 * (k + 2) + 6)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_spmv_rate(n: int, k: int, min_seconds: float, reps_per_step: int = 0):
+    """CSR SpMV of the oracle's assembled matrix on an n^3 sample; returns DoF/s and details."""
+    from oracle.discretization import Discretization
+    from seeded_inputs import random_vector
+
+    d = Discretization(n, k)
+    A = d.assemble()
+    x = random_vector(1001, d.N) * d.free_mask()
+    y = A @ x
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        y = A @ x
+        reps += 1
+        if (reps_per_step and reps >= reps_per_step) or (not reps_per_step and time.perf_counter() - t0 >= min_seconds):
+            break
+    dt = time.perf_counter() - t0
+    return d.N * reps / dt, {"n": n, "k": k, "dofs": d.N, "reps": reps, "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    sample_n, k = 8, args.k
+    from oracle.discretization import Discretization
+    from seeded_inputs import random_vector
+
+    d = Discretization(sample_n, k)
+    A = d.assemble()
+    x = random_vector(1001, d.N) * d.free_mask()
+    reps = args.ref_reps
+    for _ in range(args.warmup):
+        for _ in range(reps):
+            A @ x
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(reps):
+            A @ x
+    dt = time.perf_counter() - t0
+    rate = d.N * reps * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "GDoF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"FP64 Stokes apply, RT_{k} x DGQ_{k}, {args.n}^3 cells", "n": args.n, "k": k},
+        "cpu_baseline": {"value": rate, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                         "sample": f"CSR SpMV of the oracle's assembled matrix, {sample_n}^3 cells k={k} ({d.N} DoF), {reps} SpMVs per step"},
+        "e2e": {"value": rate, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2410_09497_gb300 import StokesMG, build, layout_sizes
+    from seeded_inputs import random_vector
+
+    if not os.path.exists(os.path.join(ROOT, "paper_2410_09497_gb300", "libstokesmg.so")):
+        build.build()
+    n, k = args.n, args.k
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    esize = 8 if dt == torch.float64 else 4
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        P = StokesMG(n, k, 1.0, stream=stream)
+        nv, npress, N = layout_sizes(n, k)
+        x_host = torch.from_numpy(random_vector(1001 + rank, N)).to(dt)
+        x = x_host.cuda()
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            P.apply(x, y)
+        stream.synchronize()
+        K = args.steps
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            time.sleep(0.3)
+            start.record(stream)
+            for i in range(K):
+                ev[i][0].record(stream)
+                P.apply_stage(0, x, y)
+                ev[i][1].record(stream)
+                P.apply_stage(1, x, y)
+            end.record(stream)
+            torch.cuda.synchronize()
+        barrier(ws)
+        t_local = start.elapsed_time(end) / 1e3
+        t_vel = sum(a.elapsed_time(b) for a, b in ev) / K / 1e3
+        t = max_over_ranks(ws, t_local)
+
+        # end to end through the public API: pinned host input, copy in, apply, copy out
+        xh = x_host.pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        for _ in range(2):
+            x.copy_(xh, non_blocking=True)
+            P.apply(x, y)
+            yh.copy_(y, non_blocking=True)
+        stream.synchronize()
+        barrier(ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            x.copy_(xh, non_blocking=True)
+            P.apply(x, y)
+            yh.copy_(y, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(ws, e0.elapsed_time(e1) / 1e3)
+        barrier(ws)
+        P.close()
+
+    value = N * ws * K / t / 1e9
+    e2e = N * ws * K / t_e2e / 1e9
+    peaks, peak_src = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    vflops = velocity_flops_per_dof(k) * 3 * nv
+    alu_peak = FP64_PEAK_TFLOPS if dt == torch.float64 else FP32_PEAK_TFLOPS
+    achieved_tf = vflops / t_vel / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    key = f"apply_velocity_k{k}_n{n}_{args.dtype}"
+    if os.path.exists(tpath):
+        traffic = json.load(open(tpath)).get(key)
+    apply_bytes = 2 * N * esize
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": t / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": f"{'FP64' if esize == 8 else 'FP32'} Stokes apply, RT_{k} x DGQ_{k}, {n}^3 cells", "n": n, "k": k,
+                   "dofs": N, "nu": 1.0, "l2": "inputs larger than L2 (x and y %d MB each)" % (N * esize // 10**6),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "kernel": "apply_velocity_kernel", "achieved": achieved_tf,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak, "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x %s FMA/clk x 2 x 2.07 GHz" % ("2 FP64" if esize == 8 else "128 FP32"),
+                     "ms_per_launch": t_vel * 1e3, "flop_per_launch": vflops},
+        "hbm_roofline": {"achieved_gbs": apply_bytes * K / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": apply_bytes * K / t / 1e9 / hbm_peak, "peak_source": peak_src,
+                         "bytes_per_step": apply_bytes},
+        "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": N * esize, "d2h_bytes_per_step": N * esize},
+        "gpu_launches": 2 * K,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, info = oracle_spmv_rate(8, k, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                                "sample": f"CSR SpMV of the oracle's assembled matrix on {info['n']}^3 cells, k={k} ({info['dofs']} DoF), {info['reps']} SpMVs in {info['seconds']:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-reps", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

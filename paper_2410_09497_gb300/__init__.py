@@ -1,0 +1,194 @@
+"""Python binding of libstokesmg (argument marshalling only).
+
+Every numerical step runs in the CUDA library behind the C ABI declared in
+include/stokesmg.h; this module only checks tensors and forwards pointers.
+There is no CPU fallback: importing works without a GPU, but constructing a
+`StokesMG` needs the compiled library and a CUDA device, and fails loudly
+otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "F64", "F32"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBNAME = "libstokesmg.so"
+
+F64, F32 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+CG_FIXED, CG_TOL = 0, 1
+_STATUS = {0: "STK_OK", -1: "STK_EINVAL", -2: "STK_ECUDA", -3: "STK_ENOMEM", -4: "STK_ENOCONV", -5: "STK_ETIMEOUT", -6: "STK_ESTATE"}
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("gmres_restart", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("local_cg_mode", ctypes.c_int),
+        ("local_cg_iters", ctypes.c_int),
+        ("local_cg_tol", ctypes.c_double),
+        ("penalty_factor", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("relres", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+        ("residuals", ctypes.c_double * 256),
+    ]
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, _LIBNAME)
+
+
+_lib = None
+
+
+def load_library():
+    """Load the in-tree libstokesmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() or python -m paper_2410_09497_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "stk_default_options": (ctypes.c_int, [ctypes.POINTER(Options)]),
+        "stk_setup": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "stk_destroy": (ctypes.c_int, [P]),
+        "stk_last_error": (ctypes.c_char_p, [P]),
+        "stk_num_levels": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
+        "stk_layout": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p, i64p, i64p]),
+        "stk_apply": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
+        "stk_residual": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P, P]),
+        "stk_apply_stage": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def layout_sizes(n: int, k: int):
+    """(n_vel_component, n_pressure, n_total) of the vector layout of an n^3 mesh at degree k."""
+    m = n * (k + 1)
+    nv = (m + 1) * m * m
+    return nv, m ** 3, 3 * nv + m ** 3
+
+
+class StokesMG:
+    """One Stokes problem on the unit cube with n cells per side and degree k.
+
+    All work is ordered on the CUDA stream that is current when the object is
+    created (or the one passed as `stream`).
+    """
+
+    def __init__(self, n: int, k: int, nu: float = 1.0, *, precision: int = PREC_FP64, gmres_restart: int = 20,
+                 max_iter: int = 200, local_cg_mode: int = CG_FIXED, local_cg_iters: int = 15,
+                 local_cg_tol: float = 1e-8, penalty_factor: float = 1.0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("StokesMG needs a CUDA device")
+        self._torch = torch
+        self.lib = load_library()
+        opt = Options()
+        self.lib.stk_default_options(ctypes.byref(opt))
+        opt.precision, opt.gmres_restart, opt.max_iter = precision, gmres_restart, max_iter
+        opt.local_cg_mode, opt.local_cg_iters, opt.local_cg_tol = local_cg_mode, local_cg_iters, local_cg_tol
+        opt.penalty_factor = penalty_factor
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        opt.stream = ctypes.c_void_p(s.cuda_stream)
+        h = ctypes.c_void_p()
+        rc = self.lib.stk_setup(int(n), int(k), float(nu), ctypes.byref(opt), ctypes.byref(h))
+        if rc != 0:
+            raise StokesError(rc, self.lib.stk_last_error(None).decode())
+        self.h = h
+        self.n, self.k, self.nu = n, k, nu
+        nl = ctypes.c_int()
+        self.lib.stk_num_levels(self.h, ctypes.byref(nl))
+        self.num_levels = nl.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise StokesError(rc, self.lib.stk_last_error(self.h).decode())
+
+    def layout(self, level: int = -1):
+        level = self._lvl(level)
+        nc = ctypes.c_int()
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.stk_layout(self.h, level, ctypes.byref(nc), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"n": nc.value, "n_vel_component": a.value, "n_pressure": b.value, "n_total": c.value}
+
+    def _lvl(self, level):
+        return level % self.num_levels if level < 0 else level
+
+    def _dt(self, t):
+        torch = self._torch
+        if t.dtype == torch.float64:
+            return F64
+        if t.dtype == torch.float32:
+            return F32
+        raise TypeError("vectors must be float64 or float32")
+
+    def _vec(self, t, level, dt=None):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("vectors must be contiguous CUDA tensors")
+        if t.numel() != self.layout(level)["n_total"]:
+            raise ValueError("vector length does not match the level's layout")
+        if dt is not None and self._dt(t) != dt:
+            raise TypeError("all vectors of a call must have the same dtype")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def apply(self, x, y, level: int = -1):
+        """y = A x on `level` (Algorithm 1)."""
+        level = self._lvl(level)
+        dt = self._dt(x)
+        self._check(self.lib.stk_apply(self.h, level, dt, self._vec(x, level), self._vec(y, level, dt)))
+        return y
+
+    def apply_stage(self, stage: int, x, y, level: int = -1):
+        """Stage 0: velocity rows of y = A x; stage 1: pressure rows."""
+        level = self._lvl(level)
+        dt = self._dt(x)
+        self._check(self.lib.stk_apply_stage(self.h, level, dt, int(stage), self._vec(x, level), self._vec(y, level, dt)))
+        return y
+
+    def residual(self, x, b, r, level: int = -1):
+        """r = b - A x on `level`."""
+        level = self._lvl(level)
+        dt = self._dt(x)
+        self._check(self.lib.stk_residual(self.h, level, dt, self._vec(x, level), self._vec(b, level, dt), self._vec(r, level, dt)))
+        return r

@@ -1,0 +1,280 @@
+// Matrix-free Stokes operator (Algorithm 1, Sec. 2.2-2.3) on a uniform
+// Cartesian mesh, in Kronecker form.
+//
+// With the diagonal Gauss mass M (entries S[a] = h w_a) of the discontinuous
+// directions, the continuous-direction stiffness KC and mass MC, the 1D
+// interior-penalty operator L (blocks LS / LLO / LHI) and the divergence
+// factor D, component c of the velocity rows is
+//     y_c = KC_c (M_d1 M_d2 u_c) + MC_c (M_d2 L_d1 u_c + M_d1 L_d2 u_c) + D_c^T (M_d1 M_d2 p)
+// (d1 < d2 the two other directions; all viscous tables carry nu), and the
+// pressure rows are  y_p = sum_c D_c (M_d1 M_d2 u_c).  This is eq. `bilinear`
+// plus eq. `weak_form` integrated exactly: face terms of eq. `bilinear` only
+// see tangential components, whose jumps live in the discontinuous directions.
+//
+// Velocity kernel: one CTA owns a tile of (d1, d2) node lines and marches
+// along the continuous direction c through a chunk of cells.  Per cell it
+// stages the k+1 new node layers of u_c (plus one cell of halo in d1 and d2)
+// in shared memory, forms t = M_d2 L_d1 u + M_d1 L_d2 u per node, and then
+// contracts along c in registers with the cell matrices KC, MC and D^T.  The
+// contribution of a cell to its upper shared node is carried to the next step,
+// so no face or node is computed twice inside a chunk; a chunk re-does only
+// the cell below it.  Pressure kernel: one thread per pressure node.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace stk {
+
+template <typename T>
+struct ApplyArgs {
+  const T* x;
+  const T* b;  // optional: y = alpha A x + b
+  T* y;
+  T alpha;
+  const CellTables<T>* tab;
+  int n, m;
+  int chunk, nchunks, ntile;
+};
+
+template <int K>
+struct ApplyCfg {
+  static constexpr int ND = K + 1, NC = K + 2;
+  static constexpr int BJ = (K == 1) ? 8 : (K == 2) ? 5 : (K == 3) ? 4 : 3;  // cells per tile side
+  static constexpr int TJ = BJ * ND;                                          // nodes per tile side
+  static constexpr int H = ND;                                                // halo width (one cell)
+  static constexpr int J = TJ + 2 * H;                                        // staged extent
+  static constexpr int NT = TJ * TJ;                                          // threads per CTA
+};
+
+template <int K, typename T>
+__global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyArgs<T> A) {
+  using Cfg = ApplyCfg<K>;
+  constexpr int ND = Cfg::ND, NC = Cfg::NC, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
+  __shared__ CellTables<T> tab;
+  extern __shared__ __align__(16) unsigned char apply_smem[];
+  T* U = reinterpret_cast<T*>(apply_smem);  // [NC][J][J] staged layers, jj fastest
+
+  const int c = blockIdx.y;
+  const int d1 = (c == 0) ? 1 : 0;
+  const int d2 = (c == 2) ? 1 : 2;
+  int bid = blockIdx.x;
+  const int chunk = bid % A.nchunks;
+  bid /= A.nchunks;
+  const int j0 = (bid % A.ntile) * TJ, l0 = (bid / A.ntile) * TJ;
+  const int tid = threadIdx.x, tj = tid % TJ, tl = tid / TJ;
+  const int m = A.m, n = A.n;
+  const int jn = j0 + tj, ln = l0 + tl;
+  const bool active = (jn < m) && (ln < m);
+
+  int64_t E[3] = {m, m, m};
+  E[c] = m + 1;
+  const int64_t st[3] = {1, E[0], E[0] * E[1]};
+  const int64_t pst[3] = {1, m, (int64_t)m * m};
+  const int64_t nvel = (int64_t)(m + 1) * m * m;
+  const T* u = A.x + c * nvel;
+  const T* p = A.x + 3 * nvel;
+  T* yc = A.y + c * nvel;
+  const T* bc = A.b ? A.b + c * nvel : nullptr;
+
+  for (int i = tid; i < (int)(sizeof(CellTables<T>) / sizeof(T)); i += NT)
+    reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(A.tab)[i];
+
+  const int cj = jn / ND, bj = jn - cj * ND, cl = ln / ND, bl = ln - cl * ND;
+  const int typej = (cj == 0) ? 1 : ((cj == n - 1) ? 2 : 0);
+  const int typel = (cl == 0) ? 1 : ((cl == n - 1) ? 2 : 0);
+  const int64_t line_off = (int64_t)jn * st[d1] + (int64_t)ln * st[d2];
+  const int64_t pline_off = (int64_t)jn * pst[d1] + (int64_t)ln * pst[d2];
+
+  const int cc0 = chunk * A.chunk;
+  const int cc1 = min(n, cc0 + A.chunk);
+  T tcar = T(0), ucar = T(0), zcar = T(0);
+  __syncthreads();
+  const T sj = tab.S[bj], sl = tab.S[bl], ss = sj * sl;
+
+  for (int cc = (cc0 > 0 ? cc0 - 1 : 0); cc < cc1; ++cc) {
+    const bool warm = cc < cc0;  // carry-only step for the cell below the chunk
+    // the first step of a CTA computes the bottom node; later steps carry it
+    const int a0 = (cc == (cc0 > 0 ? cc0 - 1 : 0)) ? 0 : 1;
+    // ---- stage layers a0..K+1 of u_c (with one cell of halo in d1 and d2)
+    const int na = NC - a0;
+    const int total = na * J * J;
+    for (int e = tid; e < total; e += NT) {
+      int a, jj, ll;
+      if (c == 0) {
+        a = e % na;
+        const int r = e / na;
+        jj = r % J;
+        ll = r / J;
+      } else if (c == 1) {
+        jj = e % J;
+        const int r = e / J;
+        a = r % na;
+        ll = r / na;
+      } else {
+        jj = e % J;
+        const int r = e / J;
+        ll = r % J;
+        a = r / J;
+      }
+      a += a0;
+      const bool hj = (jj < H) || (jj >= H + TJ), hl = (ll < H) || (ll >= H + TJ);
+      if (hj && hl) continue;  // corners are never read
+      const int gj = j0 - H + jj, gl = l0 - H + ll, ic = cc * ND + a;
+      T v = T(0);
+      if (gj >= 0 && gj < m && gl >= 0 && gl < m && ic > 0 && ic < m)
+        v = u[(int64_t)ic * st[c] + (int64_t)gj * st[d1] + (int64_t)gl * st[d2]];
+      U[(a * J + ll) * J + jj] = v;
+    }
+    __syncthreads();
+    if (active) {
+      T tv[NC], uv[NC], pv[ND], z[NC];
+      tv[0] = tcar;
+      uv[0] = ucar;
+#pragma unroll
+      for (int a = 0; a < NC; ++a) {
+        if (a < a0) continue;
+        const T* row = &U[(a * J + tl + H) * J];
+        const int bj0 = tj - bj + H;
+        T acc1 = T(0), acc2 = T(0);
+#pragma unroll
+        for (int q = 0; q < ND; ++q) {
+          acc1 += tab.LS[typej][bj * ND + q] * row[bj0 + q];
+          acc1 += tab.LLO[bj * ND + q] * row[bj0 - ND + q];
+          acc1 += tab.LHI[bj * ND + q] * row[bj0 + ND + q];
+        }
+        const int bl0 = tl - bl + H;
+#pragma unroll
+        for (int q = 0; q < ND; ++q) {
+          acc2 += tab.LS[typel][bl * ND + q] * U[(a * J + bl0 + q) * J + tj + H];
+          acc2 += tab.LLO[bl * ND + q] * U[(a * J + bl0 - ND + q) * J + tj + H];
+          acc2 += tab.LHI[bl * ND + q] * U[(a * J + bl0 + ND + q) * J + tj + H];
+        }
+        tv[a] = sl * acc1 + sj * acc2;
+        uv[a] = ss * U[(a * J + tl + H) * J + tj + H];
+      }
+#pragma unroll
+      for (int q = 0; q < ND; ++q) pv[q] = ss * p[(int64_t)(cc * ND + q) * pst[c] + pline_off];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) acc += tab.KC[i * NC + a] * uv[a] + tab.MC[i * NC + a] * tv[a];
+#pragma unroll
+        for (int q = 0; q < ND; ++q) acc += tab.D[q * NC + i] * pv[q];
+        z[i] = acc;
+      }
+      if (!warm) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+          const int ic = cc * ND + i;
+          const int64_t g = (int64_t)ic * st[c] + line_off;
+          T val = (i == 0) ? z[0] + zcar : z[i];
+          val = A.alpha * val + (bc ? bc[g] : T(0));
+          yc[g] = (ic == 0) ? T(0) : val;
+        }
+        if (cc == n - 1) yc[(int64_t)m * st[c] + line_off] = T(0);
+      }
+      tcar = tv[NC - 1];
+      ucar = uv[NC - 1];
+      zcar = z[NC - 1];
+    }
+    __syncthreads();
+  }
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(256) apply_pressure_kernel(ApplyArgs<T> A) {
+  constexpr int ND = K + 1, NC = K + 2;
+  __shared__ CellTables<T> tab;
+  for (int i = threadIdx.x; i < (int)(sizeof(CellTables<T>) / sizeof(T)); i += blockDim.x)
+    reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(A.tab)[i];
+  __syncthreads();
+  const int m = A.m;
+  const int64_t mm = (int64_t)m * m, np = mm * m;
+  const int64_t nvel = (int64_t)(m + 1) * mm;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < np; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int px = (int)(idx % m), py = (int)((idx / m) % m), pz = (int)(idx / mm);
+    const int pc[3] = {px, py, pz};
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+      int64_t E[3] = {m, m, m};
+      E[c] = m + 1;
+      const int64_t st[3] = {1, E[0], E[0] * E[1]};
+      const int cell = pc[c] / ND, q = pc[c] - cell * ND;
+      const T* u = A.x + c * nvel + (int64_t)pc[d1] * st[d1] + (int64_t)pc[d2] * st[d2];
+      T s = T(0);
+#pragma unroll
+      for (int a = 0; a < NC; ++a) {
+        const int ic = cell * ND + a;
+        const T v = (ic > 0 && ic < m) ? u[(int64_t)ic * st[c]] : T(0);
+        s += tab.D[q * NC + a] * v;
+      }
+      acc += tab.S[pc[d1] % ND] * tab.S[pc[d2] % ND] * s;
+    }
+    const int64_t g = 3 * nvel + idx;
+    A.y[g] = A.alpha * acc + (A.b ? A.b[g] : T(0));
+  }
+}
+
+template <int K, typename T>
+static cudaError_t launch_apply_k(const Level& L, const CellTables<T>* tab, const T* x, const T* b, T* y, T alpha,
+                                  int stages, cudaStream_t s) {
+  using Cfg = ApplyCfg<K>;
+  ApplyArgs<T> a;
+  a.x = x;
+  a.b = b;
+  a.y = y;
+  a.alpha = alpha;
+  a.tab = tab;
+  a.n = L.n;
+  a.m = L.m;
+  a.ntile = (L.m + Cfg::TJ - 1) / Cfg::TJ;
+  const int tiles = a.ntile * a.ntile;
+  int nch = (1216 + 3 * tiles - 1) / (3 * tiles);
+  nch = std::max(1, std::min(nch, L.n / 4 > 0 ? L.n / 4 : 1));
+  a.chunk = (L.n + nch - 1) / nch;
+  a.nchunks = (L.n + a.chunk - 1) / a.chunk;
+  dim3 grid(tiles * a.nchunks, 3);
+  const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
+  static bool attr_set = false;  // per instantiation; the attribute is per device function
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(apply_velocity_kernel<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (stages & 1) apply_velocity_kernel<K, T><<<grid, Cfg::NT, smem, s>>>(a);
+  if (stages & 2) {
+    const int64_t np = (int64_t)L.m * L.m * L.m;
+    int blocks = (int)std::min<int64_t>((np + 255) / 256, 152 * 16);
+    apply_pressure_kernel<K, T><<<blocks, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t dispatch_apply(int k, const Level& L, const CellTables<T>* tab, const T* x, const T* b, T* y,
+                                  T alpha, int stages, cudaStream_t s) {
+  switch (k) {
+    case 1: return launch_apply_k<1, T>(L, tab, x, b, y, alpha, stages, s);
+    case 2: return launch_apply_k<2, T>(L, tab, x, b, y, alpha, stages, s);
+    case 3: return launch_apply_k<3, T>(L, tab, x, b, y, alpha, stages, s);
+    case 4: return launch_apply_k<4, T>(L, tab, x, b, y, alpha, stages, s);
+    case 5: return launch_apply_k<5, T>(L, tab, x, b, y, alpha, stages, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
+                         double alpha, int stages) {
+  const Level& L = P->levels[level];
+  if (dtype == STK_F64)
+    return dispatch_apply<double>(P->k, L, L.tab64, (const double*)x, (const double*)b, (double*)y, alpha, stages,
+                                  P->stream);
+  return dispatch_apply<float>(P->k, L, L.tab32, (const float*)x, (const float*)b, (float*)y, (float)alpha, stages,
+                               P->stream);
+}
+
+}  // namespace stk
