@@ -123,6 +123,60 @@ int stk_apply_stage(stk_problem* P, int level, int dtype, int stage, const void*
  * not x. */
 int stk_residual(stk_problem* P, int level, int dtype, const void* x, const void* b, void* r);
 
+/* xf += I^up xc: prolongation from level fine_level - 1 to fine_level by the
+ * canonical embedding of the nested spaces X_{l-1} in X_l (Sec. 3).  xc has
+ * the layout of the coarser level.  xc and xf must not alias. */
+int stk_prolongate_add(stk_problem* P, int fine_level, int dtype, const void* xc, void* xf);
+
+/* rc = I^down rf: residual restriction from fine_level to fine_level - 1, the
+ * transpose of stk_prolongate_add (Sec. 3 calls it an l2-projection; the
+ * transpose is the reading used here).  rc is overwritten. */
+int stk_restrict(stk_problem* P, int fine_level, int dtype, const void* rf, void* rc);
+
+/* One step x <- S_l(x, b) of the coloured vertex-patch multiplicative Schwarz
+ * smoother (Algorithm 2, Sec. 3.1): for each of the 8 colours (ascending), the
+ * residual r = b - A x, then on every patch of the colour in parallel the
+ * local solve of Sec. 3.2 (Schur-complement CG with fast-diagonalization
+ * A_j^{-1}; stk_options.local_cg_mode / local_cg_iters / local_cg_tol) and
+ * x += R_j^T (U, P).  x is updated in place.  The first call for a dtype
+ * allocates that dtype's multigrid workspace (three vectors per level). */
+int stk_smooth(stk_problem* P, int level, int dtype, void* x, const void* b);
+
+/* x = A_0^+ b on level 0 (the exact coarse solve P_0^{-1} = A_0^{-1} of
+ * Sec. 3; the pressure null space is removed: the result is the
+ * pseudo-inverse with mean-free pressure coefficients).  Needs a 2^3 coarse
+ * mesh (n = 2^L); the first call builds the dense FP64 pseudo-inverse on the
+ * GPU (one exact patch solve per coarse DoF) and is synchronous. */
+int stk_coarse_solve(stk_problem* P, int dtype, const void* b, void* x);
+
+/* x = P_L^{-1} b on the finest level: one V-cycle with x0 = 0, one pre- and
+ * one post-smoothing step, residual restriction, exact coarse solve and
+ * prolongation (Sec. 3).  Every level runs in dtype; the coarse solve always
+ * accumulates in FP64.  Needs n = 2^L.  b and x must not alias. */
+int stk_vcycle(stk_problem* P, int dtype, const void* b, void* x);
+
+/* Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 by flexible GMRES(restart)
+ * right-preconditioned by one V-cycle, x0 = 0 (Sec. 3.3).  With
+ * STK_PREC_MIXED the V-cycle runs in FP32 inside the FP64 Krylov method, with
+ * conversions on entry and exit (Sec. 4.3).  b and x are FP64 device vectors;
+ * the returned pressure has zero L2 mean.  Synchronous on the stream: the host
+ * reads the Arnoldi coefficients every iteration.  info may be NULL.  Returns
+ * STK_ENOCONV (x holds the last iterate, info filled) when max_iter is reached
+ * first.  The first call allocates the Krylov basis (2 restart + 1 vectors). */
+int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info);
+
+/* b = right-hand side of a manufactured problem on the finest level
+ * (Sec. 3.3): velocity rows (f, phi_i) with f = -nu Laplace(u) + grad p and
+ * u = curl(psi), by the (k+3)-point Gauss rule of every cell; pressure rows
+ * and constrained rows are 0.  HOST arrays: psi_freq[3][3][3] frequencies
+ * (component, term, direction) in 1..8 and psi_amp[3][3] amplitudes of
+ *   psi_c = sum_t psi_amp[c][t] G_a(x) G_b(y) G_c(z),  G_a(s) = s^2 (1-s)^2 sin(a pi s);
+ * p_freq[3][3], p_amp[3] of  p = sum_t p_amp[t] cos(a pi x) cos(b pi y) cos(c pi z).
+ * The discrete pressure approximates -p because the velocity rows carry
+ * +(p, div v) (eq. `weak_form`).  b is a FP64 device vector, overwritten. */
+int stk_rhs(stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq, const double* p_amp,
+            double* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,13 @@ def load_library():
         "stk_apply": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
         "stk_residual": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P, P]),
         "stk_apply_stage": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
+        "stk_prolongate_add": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
+        "stk_restrict": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
+        "stk_smooth": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
+        "stk_coarse_solve": (ctypes.c_int, [P, ctypes.c_int, P, P]),
+        "stk_vcycle": (ctypes.c_int, [P, ctypes.c_int, P, P]),
+        "stk_solve": (ctypes.c_int, [P, P, P, ctypes.c_double, ctypes.POINTER(SolveInfo)]),
+        "stk_rhs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -192,3 +199,65 @@ class StokesMG:
         dt = self._dt(x)
         self._check(self.lib.stk_residual(self.h, level, dt, self._vec(x, level), self._vec(b, level, dt), self._vec(r, level, dt)))
         return r
+
+    def prolongate_add(self, xc, xf, fine_level: int = -1):
+        """xf += I^up xc (xc on fine_level - 1)."""
+        fl = self._lvl(fine_level)
+        dt = self._dt(xc)
+        self._check(self.lib.stk_prolongate_add(self.h, fl, dt, self._vec(xc, fl - 1), self._vec(xf, fl, dt)))
+        return xf
+
+    def restrict(self, rf, rc, fine_level: int = -1):
+        """rc = I^down rf (transpose of the embedding)."""
+        fl = self._lvl(fine_level)
+        dt = self._dt(rf)
+        self._check(self.lib.stk_restrict(self.h, fl, dt, self._vec(rf, fl), self._vec(rc, fl - 1, dt)))
+        return rc
+
+    def smooth(self, x, b, level: int = -1):
+        """One step of Algorithm 2 on `level`, x updated in place."""
+        level = self._lvl(level)
+        dt = self._dt(x)
+        self._check(self.lib.stk_smooth(self.h, level, dt, self._vec(x, level), self._vec(b, level, dt)))
+        return x
+
+    def coarse_solve(self, b, x):
+        """x = A_0^+ b on level 0."""
+        dt = self._dt(b)
+        self._check(self.lib.stk_coarse_solve(self.h, dt, self._vec(b, 0), self._vec(x, 0, dt)))
+        return x
+
+    def vcycle(self, b, x):
+        """x = one V-cycle applied to b (x0 = 0) on the finest level."""
+        L = self.num_levels - 1
+        dt = self._dt(b)
+        self._check(self.lib.stk_vcycle(self.h, dt, self._vec(b, L), self._vec(x, L, dt)))
+        return x
+
+    def rhs(self, coeffs: dict, b):
+        """b = (f, phi) of the manufactured solution with the given seeded coefficients (finest level)."""
+        import numpy as np
+
+        L = self.num_levels - 1
+        pf = np.ascontiguousarray(coeffs["psi_freq"], dtype=np.int32).reshape(-1)
+        pa = np.ascontiguousarray(coeffs["psi_amp"], dtype=np.float64).reshape(-1)
+        qf = np.ascontiguousarray(coeffs["p_freq"], dtype=np.int32).reshape(-1)
+        qa = np.ascontiguousarray(coeffs["p_amp"], dtype=np.float64).reshape(-1)
+        ip = ctypes.POINTER(ctypes.c_int)
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.stk_rhs(self.h, pf.ctypes.data_as(ip), pa.ctypes.data_as(dp), qf.ctypes.data_as(ip),
+                                     qa.ctypes.data_as(dp), self._vec(b, L, F64)))
+        return b
+
+    def solve(self, b, x, rtol: float = 1e-8, check: bool = True):
+        """FGMRES + V-cycle solve of A x = b (FP64 vectors); returns an info dict."""
+        L = self.num_levels - 1
+        if self._dt(b) != F64 or self._dt(x) != F64:
+            raise TypeError("solve takes float64 vectors")
+        info = SolveInfo()
+        rc = self.lib.stk_solve(self.h, self._vec(b, L), self._vec(x, L), float(rtol), ctypes.byref(info))
+        if rc != 0 and (check or rc != -4):
+            self._check(rc)
+        n = info.iterations
+        return {"iterations": n, "converged": bool(info.converged), "relres": info.relres, "nu": info.nu,
+                "seconds": info.seconds, "residuals": list(info.residuals[: min(n, 255) + 1]), "status": rc}

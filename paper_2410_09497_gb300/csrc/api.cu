@@ -40,8 +40,49 @@ int check_vec(stk_problem* P, const void* v, const char* name) {
 void free_level(stk::Level& L) {
   if (L.tab64) cudaFree(L.tab64);
   if (L.tab32) cudaFree(L.tab32);
+  if (L.ptab64) cudaFree(L.ptab64);
+  if (L.ptab32) cudaFree(L.ptab32);
   L.tab64 = nullptr;
   L.tab32 = nullptr;
+  L.ptab64 = nullptr;
+  L.ptab32 = nullptr;
+}
+
+void free_problem(stk_problem* P) {
+  for (auto& L : P->levels) free_level(L);
+  for (int d = 0; d < 2; ++d)
+    for (auto* v : {&P->mg[d].r, &P->mg[d].b, &P->mg[d].x})
+      for (void* p : *v)
+        if (p) cudaFree(p);
+  if (P->kry.V) cudaFree(P->kry.V);
+  if (P->kry.Z) cudaFree(P->kry.Z);
+  if (P->kry.partial) cudaFree(P->kry.partial);
+  if (P->kry.h) cudaFree(P->kry.h);
+  if (P->kry.h_host) cudaFreeHost(P->kry.h_host);
+  if (P->xfer64) cudaFree(P->xfer64);
+  if (P->xfer32) cudaFree(P->xfer32);
+  if (P->pmean_w) cudaFree(P->pmean_w);
+  if (P->coarse_inv) cudaFree(P->coarse_inv);
+  if (P->mixed_b) cudaFree(P->mixed_b);
+  if (P->mixed_x) cudaFree(P->mixed_x);
+  delete P;
+}
+
+int check_dtype(stk_problem* P, int dtype) {
+  if (dtype != STK_F64 && dtype != STK_F32) return fail(P, STK_EINVAL, "dtype must be STK_F64 or STK_F32");
+  return STK_OK;
+}
+
+int check_mg(stk_problem* P) {
+  if (P->levels[0].n != 2)
+    return fail(P, STK_ESTATE, "the V-cycle needs a hierarchy that coarsens to 2 cells per side (n = 2^L)");
+  return STK_OK;
+}
+
+int status_of(stk_problem* P, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return STK_OK;
+  if (e == cudaErrorMemoryAllocation) return fail(P, STK_ENOMEM, std::string(what) + ": out of device memory");
+  return cuda_fail(P, e, what);
 }
 
 }  // namespace
@@ -90,6 +131,12 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
     delete P;
     return fail(nullptr, STK_EINVAL, "penalty_factor must be positive");
   }
+  if (P->opt.gmres_restart < 1 || P->opt.gmres_restart > 60 || P->opt.max_iter < 1 || P->opt.local_cg_iters < 0 ||
+      (P->opt.precision != STK_PREC_FP64 && P->opt.precision != STK_PREC_MIXED) ||
+      (P->opt.local_cg_mode != STK_CG_FIXED && P->opt.local_cg_mode != STK_CG_TOL)) {
+    delete P;
+    return fail(nullptr, STK_EINVAL, "invalid options (restart in 1..60, max_iter >= 1, known modes)");
+  }
   P->stream = reinterpret_cast<cudaStream_t>(P->opt.stream);
   P->levels.resize(sizes.size());
   for (size_t i = 0; i < sizes.size(); ++i) {
@@ -105,14 +152,38 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
     stk::CellTables<float> h32;
     stk::fill_cell_tables(L.t1d, &h64);
     stk::fill_cell_tables(L.t1d, &h32);
+    const stk::PatchTables1D pt = stk::build_patch_tables(L.t1d);
+    stk::PatchTables<double> p64;
+    stk::PatchTables<float> p32;
+    stk::fill_patch_tables(pt, &p64);
+    stk::fill_patch_tables(pt, &p32);
     cudaError_t e = cudaMalloc(&L.tab64, sizeof(h64));
     if (e == cudaSuccess) e = cudaMalloc(&L.tab32, sizeof(h32));
+    if (e == cudaSuccess) e = cudaMalloc(&L.ptab64, sizeof(p64));
+    if (e == cudaSuccess) e = cudaMalloc(&L.ptab32, sizeof(p32));
     if (e == cudaSuccess) e = cudaMemcpy(L.tab64, &h64, sizeof(h64), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L.tab32, &h32, sizeof(h32), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.ptab64, &p64, sizeof(p64), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.ptab32, &p32, sizeof(p32), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       std::string msg = std::string("setup: ") + cudaGetErrorString(e);
-      for (auto& l : P->levels) free_level(l);
-      delete P;
+      free_problem(P);
+      return fail(nullptr, e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA, msg);
+    }
+  }
+  {
+    const std::vector<double> xt = stk::build_transfer_tables(k);
+    std::vector<float> xt32(xt.begin(), xt.end());
+    const std::vector<double>& S = P->levels.back().t1d.S;
+    cudaError_t e = cudaMalloc(&P->xfer64, sizeof(double) * xt.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->xfer32, sizeof(float) * xt.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->pmean_w, sizeof(double) * S.size());
+    if (e == cudaSuccess) e = cudaMemcpy(P->xfer64, xt.data(), sizeof(double) * xt.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->xfer32, xt32.data(), sizeof(float) * xt.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->pmean_w, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      std::string msg = std::string("setup: ") + cudaGetErrorString(e);
+      free_problem(P);
       return fail(nullptr, e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA, msg);
     }
   }
@@ -123,8 +194,7 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
 int stk_destroy(stk_problem* P) {
   if (!P) return STK_OK;
   cudaStreamSynchronize(P->stream);
-  for (auto& L : P->levels) free_level(L);
-  delete P;
+  free_problem(P);
   return STK_OK;
 }
 
@@ -180,6 +250,73 @@ int stk_residual(stk_problem* P, int level, int dtype, const void* x, const void
   cudaError_t e = stk::launch_apply(P, level, dtype, x, b, r, -1.0);
   if (e != cudaSuccess) return cuda_fail(P, e, "residual");
   return STK_OK;
+}
+
+int stk_prolongate_add(stk_problem* P, int fine_level, int dtype, const void* xc, void* xf) {
+  int rc = check_level(P, fine_level);
+  if (rc) return rc;
+  if (fine_level == 0) return fail(P, STK_EINVAL, "level 0 has no coarser level");
+  if ((rc = check_dtype(P, dtype)) || (rc = check_vec(P, xc, "xc")) || (rc = check_vec(P, xf, "xf"))) return rc;
+  return status_of(P, stk::launch_prolongate_add(P, fine_level, dtype, xc, xf), "prolongate_add");
+}
+
+int stk_restrict(stk_problem* P, int fine_level, int dtype, const void* rf, void* rc_out) {
+  int rc = check_level(P, fine_level);
+  if (rc) return rc;
+  if (fine_level == 0) return fail(P, STK_EINVAL, "level 0 has no coarser level");
+  if ((rc = check_dtype(P, dtype)) || (rc = check_vec(P, rf, "rf")) || (rc = check_vec(P, rc_out, "rc"))) return rc;
+  return status_of(P, stk::launch_restrict(P, fine_level, dtype, rf, rc_out), "restrict");
+}
+
+int stk_smooth(stk_problem* P, int level, int dtype, void* x, const void* b) {
+  int rc = check_level(P, level);
+  if (rc) return rc;
+  if ((rc = check_dtype(P, dtype)) || (rc = check_vec(P, x, "x")) || (rc = check_vec(P, b, "b"))) return rc;
+  if (x == b) return fail(P, STK_EINVAL, "x and b must not alias");
+  return status_of(P, stk::run_smooth(P, level, dtype, x, b), "smooth");
+}
+
+int stk_coarse_solve(stk_problem* P, int dtype, const void* b, void* x) {
+  if (!P) return STK_EINVAL;
+  int rc;
+  if ((rc = check_mg(P)) || (rc = check_dtype(P, dtype)) || (rc = check_vec(P, b, "b")) || (rc = check_vec(P, x, "x")))
+    return rc;
+  if (x == b) return fail(P, STK_EINVAL, "x and b must not alias");
+  return status_of(P, stk::run_coarse_solve(P, dtype, b, x), "coarse_solve");
+}
+
+int stk_vcycle(stk_problem* P, int dtype, const void* b, void* x) {
+  if (!P) return STK_EINVAL;
+  int rc;
+  if ((rc = check_mg(P)) || (rc = check_dtype(P, dtype)) || (rc = check_vec(P, b, "b")) || (rc = check_vec(P, x, "x")))
+    return rc;
+  if (x == b) return fail(P, STK_EINVAL, "x and b must not alias");
+  return status_of(P, stk::run_vcycle(P, dtype, b, x), "vcycle");
+}
+
+int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info) {
+  if (!P) return STK_EINVAL;
+  int rc;
+  if ((rc = check_mg(P)) || (rc = check_vec(P, b, "b")) || (rc = check_vec(P, x, "x"))) return rc;
+  if ((const void*)x == (const void*)b) return fail(P, STK_EINVAL, "x and b must not alias");
+  if (!(rtol > 0.0)) return fail(P, STK_EINVAL, "rtol must be positive");
+  std::string err;
+  rc = stk::run_solve(P, b, x, rtol, info, err);
+  if (rc) return fail(P, rc, err);
+  return STK_OK;
+}
+
+int stk_rhs(stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq, const double* p_amp,
+            double* b) {
+  if (!P) return STK_EINVAL;
+  if (!psi_freq || !psi_amp || !p_freq || !p_amp) return fail(P, STK_EINVAL, "coefficient arrays must not be NULL");
+  int rc = check_vec(P, b, "b");
+  if (rc) return rc;
+  for (int i = 0; i < 27; ++i)
+    if (psi_freq[i] < 1 || psi_freq[i] > 8) return fail(P, STK_EINVAL, "psi frequencies must be in 1..8");
+  for (int i = 0; i < 9; ++i)
+    if (p_freq[i] < 1 || p_freq[i] > 8) return fail(P, STK_EINVAL, "pressure frequencies must be in 1..8");
+  return status_of(P, stk::launch_rhs(P, psi_freq, psi_amp, p_freq, p_amp, b), "rhs");
 }
 
 }  // extern "C"

@@ -18,8 +18,8 @@ constexpr int kMaxD = kMaxDegree + 1;  // nodes of a cell in a discontinuous dir
 // 1D cell matrices of one level (Sec. 2.3 and Sec. 3.2), row-major, in the
 // precision of the kernel that reads them.  Layout is fixed so a kernel can
 // copy the whole struct into shared memory.
-//   KC[i][j]  nu * int phi_i' phi_j'        continuous (Gauss-Lobatto) basis, (k+2)^2
-//   MC[i][j]  nu * int phi_i  phi_j         continuous basis, (k+2)^2
+//   KC[i][j]  nu * int phi_i' phi_j'      continuous (Gauss-Lobatto) basis, (k+2)^2
+//   MC[i][j]  int phi_i phi_j (no nu)     continuous basis, (k+2)^2
 //   D[q][a]   int psi_q phi_a'              pressure (Gauss) x continuous derivative, (k+1)(k+2)
 //   LS[t][b][c] nu * 1D interior-penalty block of a cell with itself:
 //             t = 0 interior cell, 1 first cell (face x = 0), 2 last cell (x = 1)
@@ -47,6 +47,41 @@ struct Tables1D {
   std::vector<double> S;
 };
 
+constexpr int kMaxPC = 2 * kMaxDegree + 1;  // patch-interior nodes, continuous direction
+constexpr int kMaxPD = 2 * kMaxDegree + 2;  // patch nodes, discontinuous direction
+
+// Fast-diagonalization data of the vertex-patch local solver (Sec. 3.2) for
+// one level, in kernel precision:
+//   SC[i][j], LC[j]  eigenvectors (columns) / eigenvalues of the continuous direction
+//   SD[t][i][j], LD[t][j]  the same for a discontinuous direction of boundary type t
+//   DL[q][a]  local divergence factor (2k+2 pressure x 2k+1 velocity nodes)
+//   W[j]      diagonal patch mass of a discontinuous direction
+template <typename T>
+struct PatchTables {
+  T SC[kMaxPC * kMaxPC];
+  T LC[kMaxPC];
+  T SD[4][kMaxPD * kMaxPD];
+  T LD[4][kMaxPD];
+  T DL[kMaxPD * kMaxPC];
+  T W[kMaxPD];
+  T inv_nu;
+};
+
+struct PatchTables1D {
+  int k = 0;
+  double nu = 1.0;
+  std::vector<double> SC, LC, SD[4], LD[4], DL, W;
+};
+
+void generalized_eigen(int n, const std::vector<double>& K, const std::vector<double>& M, std::vector<double>& S,
+                       std::vector<double>& lam);
+struct Tables1D;
+PatchTables1D build_patch_tables(const Tables1D& t);
+template <typename T>
+void fill_patch_tables(const PatchTables1D& p, PatchTables<T>* out);
+// PC[2][k+2][k+2] followed by PD[2][k+1][k+1] (transfer.cu)
+std::vector<double> build_transfer_tables(int k);
+
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 void gauss_lobatto(int n, std::vector<double>& x, std::vector<double>& w);
 // values V[i*np+q] = l_i(t_q) and derivatives Dv[i*np+q] = l_i'(t_q)
@@ -64,6 +99,22 @@ struct Level {
   Tables1D t1d;
   CellTables<double>* tab64 = nullptr;  // device
   CellTables<float>* tab32 = nullptr;   // device
+  PatchTables<double>* ptab64 = nullptr;  // device
+  PatchTables<float>* ptab32 = nullptr;   // device
+};
+
+struct MgWork {
+  bool ready = false;
+  std::vector<void*> r, b, x;  // per level: residual, coarse rhs, coarse solution
+};
+
+struct KrylovWork {
+  bool ready = false;
+  double* V = nullptr;  // (restart + 1) basis vectors
+  double* Z = nullptr;  // restart preconditioned vectors
+  double* partial = nullptr;
+  double* h = nullptr;
+  double* h_host = nullptr;  // pinned
 };
 
 }  // namespace stk
@@ -74,6 +125,14 @@ struct stk_problem {
   stk_options opt{};
   cudaStream_t stream = nullptr;
   std::vector<stk::Level> levels;  // [0] coarsest
+  double* xfer64 = nullptr;        // device transfer tables (build_transfer_tables)
+  float* xfer32 = nullptr;
+  double* pmean_w = nullptr;       // device Gauss weights x h of the finest level (pressure mean)
+  double* coarse_inv = nullptr;    // dense pseudo-inverse of the 2^3 coarse problem, patch order
+  stk::MgWork mg[2];               // [STK_F64], [STK_F32]
+  stk::KrylovWork kry;
+  void* mixed_b = nullptr;         // FP32 copies of the finest rhs / solution (mixed precision)
+  void* mixed_x = nullptr;
   std::string err;
 };
 
@@ -83,5 +142,23 @@ namespace stk {
 // stages: bit 0 = velocity rows, bit 1 = pressure rows (3 = the whole operator).
 cudaError_t launch_apply(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
                          double alpha, int stages = 3);
+// xf += I^up xc (xc on fine_level - 1); rc = I^down rf (rc is overwritten).
+cudaError_t launch_prolongate_add(const stk_problem* P, int fine_level, int dtype, const void* xc, void* xf);
+cudaError_t launch_restrict(const stk_problem* P, int fine_level, int dtype, const void* rf, void* rc);
+// smoother.cu
+int patch_local_size(int k);
+cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x);
+cudaError_t launch_coarse_columns(const stk_problem* P, double* cols, int max_iter, double tol);
+cudaError_t launch_coarse_solve(const stk_problem* P, int dtype, const void* b, void* x);
+// solver.cu
+cudaError_t ensure_mg_workspace(stk_problem* P, int dtype);
+cudaError_t ensure_coarse(stk_problem* P);
+cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void* b);
+cudaError_t run_vcycle(stk_problem* P, int dtype, const void* b, void* x);
+cudaError_t run_coarse_solve(stk_problem* P, int dtype, const void* b, void* x);
+int run_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info, std::string& err);
+// rhs.cu
+cudaError_t launch_rhs(const stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq,
+                       const double* p_amp, double* b);
 
 }  // namespace stk

@@ -131,7 +131,7 @@ Tables1D build_tables(int k, double h, double nu, double penalty_factor) {
         s2 += wq[q] * VC[i * nq + q] * VC[j * nq + q];
       }
       T.KC[i * nc + j] = nu * s1 / h;
-      T.MC[i * nc + j] = nu * s2 * h;
+      T.MC[i * nc + j] = s2 * h;  // plain mass: it multiplies the nu-scaled 1D penalty operator
     }
   for (int a = 0; a < nd; ++a)
     for (int i = 0; i < nc; ++i) {

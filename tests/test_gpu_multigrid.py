@@ -1,0 +1,158 @@
+"""GPU parity of the multigrid pieces against the CPU oracle, through the C ABI.
+
+transfers (Sec. 3), one smoothing step of Algorithm 2 with the Schur-CG local
+solver (fixed step count, as the oracle's restatement) and with a converged
+CG against the Direct (dense LU) local solver, the exact coarse solve, one
+V-cycle, and the FGMRES solve in FP64 and mixed precision.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.discretization import Discretization
+from oracle.manufactured import Manufactured, rhs
+from oracle.multigrid import Hierarchy
+from oracle.transfer import prolongation
+from seeded_inputs import manufactured_coefficients, random_vector
+
+pytestmark = pytest.mark.gpu
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def dev(x, dtype=None):
+    import torch
+
+    t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return t.to(dtype) if dtype is not None else t
+
+
+@pytest.mark.parametrize("k,nf", [(1, 4), (1, 8), (2, 4), (3, 8), (4, 4), (5, 4)])
+def test_transfers(stk, k, nf):
+    import torch
+
+    C, F = Discretization(nf // 2, k), Discretization(nf, k)
+    Pm = prolongation(C, F)
+    P = stk.StokesMG(nf, k)
+    L = P.num_levels - 1
+    xc = random_vector(300 + k, C.N) * C.free_mask()
+    xf0 = random_vector(400 + k, F.N) * F.free_mask()
+    out = dev(xf0.copy())
+    P.prolongate_add(dev(xc), out)
+    assert relerr(out.cpu().numpy(), xf0 + Pm @ xc) <= 1e-12
+    rf = random_vector(500 + k, F.N)
+    rc = torch.full((C.N,), float("nan"), dtype=torch.float64, device="cuda")
+    P.restrict(dev(rf), rc)
+    assert relerr(rc.cpu().numpy(), Pm.T @ (rf * F.free_mask())) <= 1e-12
+    # FP32
+    out32 = dev(xf0.astype(np.float32))
+    P.prolongate_add(dev(xc.astype(np.float32)), out32)
+    ref = xf0.astype(np.float32).astype(float) + Pm @ xc.astype(np.float32).astype(float)
+    assert relerr(out32.cpu().numpy().astype(float), ref) <= 1e-5
+    rc32 = torch.empty(C.N, dtype=torch.float32, device="cuda")
+    P.restrict(dev(rf.astype(np.float32)), rc32)
+    assert relerr(rc32.cpu().numpy().astype(float), Pm.T @ (rf.astype(np.float32).astype(float) * F.free_mask())) <= 1e-5
+    P.close()
+
+
+@pytest.mark.parametrize("n,k,iters", [(4, 1, 15), (4, 2, 15), (6, 2, 15), (4, 3, 15), (4, 4, 8), (8, 2, 5)])
+def test_smooth_fixed_cg_matches_oracle(stk, n, k, iters):
+    H = Hierarchy(n, k, local=("schur", iters))
+    d = H.levels[-1].disc
+    x0 = random_vector(600 + n + k, d.N) * d.free_mask()
+    b = random_vector(700 + n + k, d.N) * d.free_mask()
+    ref = H.smooth(len(H.levels) - 1, x0, b)
+    P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=iters)
+    x = dev(x0.copy())
+    P.smooth(x, dev(b))
+    assert relerr(x.cpu().numpy(), ref) <= 1e-11
+    # FP32 smoother against the same FP64 reference
+    x32 = dev(x0.astype(np.float32))
+    P.smooth(x32, dev(b.astype(np.float32)))
+    assert relerr(x32.cpu().numpy().astype(float), ref) <= 2e-4
+    P.close()
+
+
+@pytest.mark.parametrize("n,k", [(3, 2), (4, 3), (6, 1)])
+def test_smooth_converged_cg_equals_direct(stk, n, k):
+    H = Hierarchy(n, k, local="lu")
+    d = H.levels[-1].disc
+    x0 = random_vector(800 + n + k, d.N) * d.free_mask()
+    b = random_vector(900 + n + k, d.N) * d.free_mask()
+    ref = H.smooth(len(H.levels) - 1, x0, b)
+    P = stk.StokesMG(n, k, local_cg_mode=stk.CG_TOL, local_cg_iters=2000, local_cg_tol=1e-14)
+    x = dev(x0.copy())
+    P.smooth(x, dev(b))
+    assert relerr(x.cpu().numpy(), ref) <= 1e-10
+    P.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_coarse_solve_is_pseudo_inverse(stk, k):
+    H = Hierarchy(2, k)
+    d = H.levels[0].disc
+    b = random_vector(1100 + k, d.N) * d.free_mask()
+    ref = H.coarse_solve(b)
+    P = stk.StokesMG(2, k)
+    x = dev(np.full(d.N, np.nan))
+    P.coarse_solve(dev(b), x)
+    xs = x.cpu().numpy()
+    # both are mean-free in the pressure coefficients; compare directly
+    assert relerr(xs, ref) <= 1e-10
+    P.close()
+
+
+@pytest.mark.parametrize("n,k", [(4, 2), (8, 1), (4, 3), (8, 2)])
+def test_vcycle_matches_oracle(stk, n, k):
+    H = Hierarchy(n, k, local=("schur", 15))
+    d = H.levels[-1].disc
+    b = random_vector(1200 + n + k, d.N) * d.free_mask()
+    ref = H.vcycle(b)
+    P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
+    x = dev(np.full(d.N, np.nan))
+    P.vcycle(dev(b), x)
+    assert relerr(x.cpu().numpy(), ref) <= 1e-10
+    x32 = dev(np.full(d.N, np.nan, dtype=np.float32))
+    P.vcycle(dev(b.astype(np.float32)), x32)
+    assert relerr(x32.cpu().numpy().astype(float), ref) <= 5e-4
+    P.close()
+
+
+@pytest.mark.parametrize("n,k", [(4, 2), (8, 2), (4, 3)])
+def test_solve_matches_oracle(stk, n, k):
+    man = Manufactured(manufactured_coefficients(0))
+    H = Hierarchy(n, k, local=("schur", 15))
+    d = H.levels[-1].disc
+    b = rhs(d, man)
+    ref, info_ref = H.solve(b, tol=1e-8)
+    for prec in (stk.PREC_FP64, stk.PREC_MIXED):
+        P = stk.StokesMG(n, k, precision=prec, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
+        x = dev(np.zeros(d.N))
+        info = P.solve(dev(b), x, rtol=1e-8)
+        xs = x.cpu().numpy()
+        A = H.levels[-1].A
+        true_rel = np.linalg.norm(b - A @ xs) / np.linalg.norm(b)
+        assert info["converged"] and true_rel <= 1e-8
+        if prec == stk.PREC_FP64:
+            assert info["iterations"] == info_ref["iterations"]
+            assert relerr(xs, ref) <= 1e-9
+        else:
+            assert abs(info["iterations"] - info_ref["iterations"]) <= 1
+            assert relerr(xs, ref) <= 1e-6
+        P.close()
+
+
+@pytest.mark.parametrize("n,k,nu", [(2, 1, 1.0), (4, 2, 1.0), (4, 3, 0.6), (3, 4, 1.0), (2, 5, 1.0)])
+def test_rhs_matches_oracle(stk, n, k, nu):
+    import torch
+
+    coef = manufactured_coefficients(17)
+    d = Discretization(n, k, nu=nu)
+    ref = rhs(d, Manufactured(coef, nu=nu))
+    P = stk.StokesMG(n, k, nu)
+    b = torch.full((d.N,), float("nan"), dtype=torch.float64, device="cuda")
+    P.rhs(coef, b)
+    assert relerr(b.cpu().numpy(), ref) <= 1e-12
+    P.close()
