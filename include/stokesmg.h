@@ -177,6 +177,21 @@ int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve
 int stk_rhs(stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq, const double* p_amp,
             double* b);
 
+/* stk_smooth without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not call cudaMalloc, such as
+ * code recording into a CUDA graph (no allocation during stream capture), a
+ * framework whose memory pool must own every device allocation, or a
+ * real-time loop that cannot absorb an allocation stall.  Same kernels, same
+ * order and same result as stk_smooth; the colour residual lives in a 32 MiB
+ * array of device global memory built into the library (every GPU that loads
+ * the library holds it until exit), so the level must have
+ * N * sizeof(dtype) <= 33554432 bytes, else STK_EINVAL with a message.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race and must be ordered by
+ * the caller.  Nothing in the array needs clearing between calls. */
+int stk_smooth_static(stk_problem* P, int level, int dtype, void* x, const void* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ def load_library():
         "stk_vcycle": (ctypes.c_int, [P, ctypes.c_int, P, P]),
         "stk_solve": (ctypes.c_int, [P, P, P, ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_rhs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P]),
+        "stk_smooth_static": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -219,6 +220,13 @@ class StokesMG:
         level = self._lvl(level)
         dt = self._dt(x)
         self._check(self.lib.stk_smooth(self.h, level, dt, self._vec(x, level), self._vec(b, level, dt)))
+        return x
+
+    def smooth_static(self, x, b, level: int = -1):
+        """stk_smooth without device allocation (residual in the library's static 32 MiB array)."""
+        level = self._lvl(level)
+        dt = self._dt(x)
+        self._check(self.lib.stk_smooth_static(self.h, level, dt, self._vec(x, level), self._vec(b, level, dt)))
         return x
 
     def coarse_solve(self, b, x):
