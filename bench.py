@@ -164,6 +164,55 @@ def oracle_spmv_rate(n: int, k: int, min_seconds: float, reps_per_step: int = 0)
     return d.N * reps / dt, {"n": n, "k": k, "dofs": d.N, "reps": reps, "seconds": dt}
 
 
+def oracle_solve_rate(n: int, k: int):
+    """The oracle's FGMRES + V-cycle solve (dense-LU patch solves) to 1e-8 on an n^3 sample."""
+    from oracle.manufactured import Manufactured, rhs
+    from oracle.multigrid import Hierarchy
+    from seeded_inputs import manufactured_coefficients
+
+    H = Hierarchy(n, k, local=("schur", 15))
+    d = H.levels[-1].disc
+    b = rhs(d, Manufactured(manufactured_coefficients(3000)))
+    t0 = time.perf_counter()
+    _, info = H.solve(b, tol=1e-8)
+    dt = time.perf_counter() - t0
+    return {"value": dt / (d.N / 1e6), "unit": "s/MDoF", "cores": 1, "kind": "oracle",
+            "sample": f"oracle FGMRES(20) + V-cycle (Schur-CG 15 local solver) to 1e-8 on {n}^3 cells, k={k} ({d.N} DoF), {info['iterations']} iterations, {dt:.1f} s"}
+
+
+def run_solve_pair(args, stream, ws):
+    """Mixed-precision and FP64 multigrid solves of the seeded manufactured problem to 1e-8."""
+    import torch
+
+    from paper_2410_09497_gb300 import PREC_FP64, PREC_MIXED, StokesMG
+    from seeded_inputs import manufactured_coefficients
+
+    n, k = args.solve_n, args.solve_k
+    out = {"workload": f"manufactured Stokes solve, RT_{k} x DGQ_{k}, {n}^3 cells, FGMRES(20) + V-cycle to 1e-8",
+           "unit": "s/MDoF", "higher_is_better": False}
+    coef = manufactured_coefficients(3000)
+    for name, prec in (("mixed", PREC_MIXED), ("fp64", PREC_FP64)):
+        with torch.cuda.stream(stream):
+            P = StokesMG(n, k, 1.0, precision=prec, stream=stream)
+            N = P.layout()["n_total"]
+            b = torch.empty(N, dtype=torch.float64, device="cuda")
+            x = torch.zeros_like(b)
+            P.rhs(coef, b)
+            P.solve(b, x, 1e-8)  # warm-up: workspace, coarse pseudo-inverse
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+            info = P.solve(b, x, 1e-8)
+            torch.cuda.synchronize()
+            t = max_over_ranks(ws, time.perf_counter() - t0)
+            P.close()
+        out[name] = {"seconds": t, "s_per_MDoF": t / (N / 1e6), "dofs": N, "iterations": info["iterations"],
+                     "nu": info["nu"], "relres": info["relres"], "converged": info["converged"]}
+    out["mixed_speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["value"] = out["mixed"]["s_per_MDoF"]
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -294,10 +343,14 @@ def run_ours(args):
         "gpu_launches": 2 * K,
         "clocks": clk.summary(),
     }
+    if args.solve_n > 0:
+        line["solve"] = run_solve_pair(args, stream, ws)
     if rank == 0 and not args.no_cpu_baseline:
         rate, info = oracle_spmv_rate(8, k, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
                                 "sample": f"CSR SpMV of the oracle's assembled matrix on {info['n']}^3 cells, k={k} ({info['dofs']} DoF), {info['reps']} SpMVs in {info['seconds']:.1f} s"}
+        if args.solve_n > 0:
+            line["solve"]["cpu_baseline"] = oracle_solve_rate(4, args.solve_k)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -319,6 +372,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-reps", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-n", type=int, default=64, help="mesh of the mixed-vs-FP64 solve sub-benchmark (0: skip)")
+    ap.add_argument("--solve-k", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

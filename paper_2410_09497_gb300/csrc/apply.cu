@@ -46,6 +46,43 @@ struct ApplyCfg {
   static constexpr int NT = TJ * TJ;                                          // threads per CTA
 };
 
+// Stage NA node layers a0 .. a0+NA-1 of cell cc along c into U[a][ll][jj],
+// one cell of halo in d1 and d2 (corners skipped: never read).  Global memory
+// is walked in its own order (x fastest) so that loads coalesce.
+template <int K, typename T, int NA>
+__device__ __forceinline__ void stage_layers(T* __restrict__ U, const T* __restrict__ u, int a0, int c, int cc,
+                                             int j0, int l0, int m, int64_t sc, int64_t s1, int64_t s2) {
+  using Cfg = ApplyCfg<K>;
+  constexpr int ND = Cfg::ND, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
+  constexpr int total = NA * J * J;
+  for (int e = threadIdx.x; e < total; e += NT) {
+    int a, jj, ll;
+    if (c == 0) {
+      a = e % NA;
+      const int r = e / NA;
+      jj = r % J;
+      ll = r / J;
+    } else if (c == 1) {
+      jj = e % J;
+      const int r = e / J;
+      a = r % NA;
+      ll = r / NA;
+    } else {
+      jj = e % J;
+      const int r = e / J;
+      ll = r % J;
+      a = r / J;
+    }
+    a += a0;
+    const bool hj = (jj < H) || (jj >= H + TJ), hl = (ll < H) || (ll >= H + TJ);
+    if (hj && hl) continue;
+    const int gj = j0 - H + jj, gl = l0 - H + ll, ic = cc * ND + a;
+    T v = T(0);
+    if (gj >= 0 && gj < m && gl >= 0 && gl < m && ic > 0 && ic < m) v = u[ic * sc + gj * s1 + gl * s2];
+    U[(a * J + ll) * J + jj] = v;
+  }
+}
+
 template <int K, typename T>
 __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyArgs<T> A) {
   using Cfg = ApplyCfg<K>;
@@ -66,10 +103,15 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
   const int jn = j0 + tj, ln = l0 + tl;
   const bool active = (jn < m) && (ln < m);
 
-  int64_t E[3] = {m, m, m};
-  E[c] = m + 1;
-  const int64_t st[3] = {1, E[0], E[0] * E[1]};
-  const int64_t pst[3] = {1, m, (int64_t)m * m};
+  // strides of u_c along c, d1, d2 (x-fastest grid, extent m+1 along c) and of p
+  const int64_t E0 = (c == 0) ? m + 1 : m, E1 = (c == 1) ? m + 1 : m;
+  const int64_t sc = (c == 0) ? 1 : (c == 1 ? E0 : E0 * E1);
+  const int64_t s1 = (d1 == 0) ? 1 : E0;
+  const int64_t s2 = (d2 == 1) ? E0 : E0 * E1;
+  const int64_t mm = (int64_t)m * m;
+  const int64_t psc = (c == 0) ? 1 : (c == 1 ? m : mm);
+  const int64_t ps1 = (d1 == 0) ? 1 : m;
+  const int64_t ps2 = (d2 == 1) ? m : mm;
   const int64_t nvel = (int64_t)(m + 1) * m * m;
   const T* u = A.x + c * nvel;
   const T* p = A.x + 3 * nvel;
@@ -82,8 +124,8 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
   const int cj = jn / ND, bj = jn - cj * ND, cl = ln / ND, bl = ln - cl * ND;
   const int typej = (cj == 0) ? 1 : ((cj == n - 1) ? 2 : 0);
   const int typel = (cl == 0) ? 1 : ((cl == n - 1) ? 2 : 0);
-  const int64_t line_off = (int64_t)jn * st[d1] + (int64_t)ln * st[d2];
-  const int64_t pline_off = (int64_t)jn * pst[d1] + (int64_t)ln * pst[d2];
+  const int64_t line_off = (int64_t)jn * s1 + (int64_t)ln * s2;
+  const int64_t pline_off = (int64_t)jn * ps1 + (int64_t)ln * ps2;
 
   const int cc0 = chunk * A.chunk;
   const int cc1 = min(n, cc0 + A.chunk);
@@ -96,35 +138,10 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
     // the first step of a CTA computes the bottom node; later steps carry it
     const int a0 = (cc == (cc0 > 0 ? cc0 - 1 : 0)) ? 0 : 1;
     // ---- stage layers a0..K+1 of u_c (with one cell of halo in d1 and d2)
-    const int na = NC - a0;
-    const int total = na * J * J;
-    for (int e = tid; e < total; e += NT) {
-      int a, jj, ll;
-      if (c == 0) {
-        a = e % na;
-        const int r = e / na;
-        jj = r % J;
-        ll = r / J;
-      } else if (c == 1) {
-        jj = e % J;
-        const int r = e / J;
-        a = r % na;
-        ll = r / na;
-      } else {
-        jj = e % J;
-        const int r = e / J;
-        ll = r % J;
-        a = r / J;
-      }
-      a += a0;
-      const bool hj = (jj < H) || (jj >= H + TJ), hl = (ll < H) || (ll >= H + TJ);
-      if (hj && hl) continue;  // corners are never read
-      const int gj = j0 - H + jj, gl = l0 - H + ll, ic = cc * ND + a;
-      T v = T(0);
-      if (gj >= 0 && gj < m && gl >= 0 && gl < m && ic > 0 && ic < m)
-        v = u[(int64_t)ic * st[c] + (int64_t)gj * st[d1] + (int64_t)gl * st[d2]];
-      U[(a * J + ll) * J + jj] = v;
-    }
+    if (a0 == 0)
+      stage_layers<K, T, NC>(U, u, 0, c, cc, j0, l0, m, sc, s1, s2);
+    else
+      stage_layers<K, T, ND>(U, u, 1, c, cc, j0, l0, m, sc, s1, s2);
     __syncthreads();
     if (active) {
       T tv[NC], uv[NC], pv[ND], z[NC];
@@ -153,7 +170,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
         uv[a] = ss * U[(a * J + tl + H) * J + tj + H];
       }
 #pragma unroll
-      for (int q = 0; q < ND; ++q) pv[q] = ss * p[(int64_t)(cc * ND + q) * pst[c] + pline_off];
+      for (int q = 0; q < ND; ++q) pv[q] = ss * p[(int64_t)(cc * ND + q) * psc + pline_off];
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
         T acc = T(0);
@@ -167,12 +184,12 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
 #pragma unroll
         for (int i = 0; i < ND; ++i) {
           const int ic = cc * ND + i;
-          const int64_t g = (int64_t)ic * st[c] + line_off;
+          const int64_t g = (int64_t)ic * sc + line_off;
           T val = (i == 0) ? z[0] + zcar : z[i];
           val = A.alpha * val + (bc ? bc[g] : T(0));
           yc[g] = (ic == 0) ? T(0) : val;
         }
-        if (cc == n - 1) yc[(int64_t)m * st[c] + line_off] = T(0);
+        if (cc == n - 1) yc[(int64_t)m * sc + line_off] = T(0);
       }
       tcar = tv[NC - 1];
       ucar = uv[NC - 1];

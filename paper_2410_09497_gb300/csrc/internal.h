@@ -56,6 +56,8 @@ constexpr int kMaxPD = 2 * kMaxDegree + 2;  // patch nodes, discontinuous direct
 //   SD[t][i][j], LD[t][j]  the same for a discontinuous direction of boundary type t
 //   DL[q][a]  local divergence factor (2k+2 pressure x 2k+1 velocity nodes)
 //   W[j]      diagonal patch mass of a discontinuous direction
+//   EC[q][j]  = sum_a DL[q][a] SC[a][j]: the divergence factor in the eigenbasis
+//   FM[t][q][j] = W[q] SD[t][q][j]: the mass factor in the eigenbasis
 template <typename T>
 struct PatchTables {
   T SC[kMaxPC * kMaxPC];
@@ -64,6 +66,8 @@ struct PatchTables {
   T LD[4][kMaxPD];
   T DL[kMaxPD * kMaxPC];
   T W[kMaxPD];
+  T EC[kMaxPD * kMaxPC];
+  T FM[4][kMaxPD * kMaxPD];
   T inv_nu;
 };
 

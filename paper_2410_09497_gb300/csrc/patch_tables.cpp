@@ -173,6 +173,16 @@ void fill_patch_tables(const PatchTables1D& p, PatchTables<T>* out) {
   }
   for (int i = 0; i < npd * npc; ++i) out->DL[i] = (T)p.DL[i];
   for (int i = 0; i < npd; ++i) out->W[i] = (T)p.W[i];
+  // B_c (S_c (x) S_d1 (x) S_d2) = (DL SC) (x) (W SD) (x) (W SD): the Schur operator in the eigenbasis
+  for (int q = 0; q < npd; ++q)
+    for (int j = 0; j < npc; ++j) {
+      double s = 0.0;
+      for (int a = 0; a < npc; ++a) s += p.DL[q * npc + a] * p.SC[a * npc + j];
+      out->EC[q * npc + j] = (T)s;
+    }
+  for (int t = 0; t < 4; ++t)
+    for (int q = 0; q < npd; ++q)
+      for (int j = 0; j < npd; ++j) out->FM[t][q * npd + j] = (T)(p.W[q] * p.SD[t][q * npd + j]);
   out->inv_nu = (T)(1.0 / p.nu);
 }
 

@@ -10,12 +10,20 @@
 //           S = B A^{-1} B^T, then U = A^{-1} (F - B^T P)
 //   scatter x += R_j^T (U, P)
 // The patches of one colour share no DoF, so the scatter needs no atomics.
-// A^{-1} of each velocity component is applied as
-//   (1/nu) (S_x (x) S_y (x) S_z) diag(1 / (lam_x + lam_y + lam_z)) (S_x (x) S_y (x) S_z)^T
-// (eq. `inverse2d` in 3D): three forward line transforms, a diagonal scale,
-// three backward line transforms, all in shared memory.  B and B^T are the
-// local divergence factor D_loc along the component's continuous direction
-// scaled by the diagonal Gauss masses of the other two (eq. `b`).
+//
+// Fast diagonalization (eq. `inverse2d`, eq. `fast_inverse` in 3D): per
+// velocity component c,  A_c^{-1} = (1/nu) S_c Lam_c^{-1} S_c^T  with
+// S_c = S_x (x) S_y (x) S_z (continuous-direction eigenvectors along c,
+// discontinuous ones along the other two).  Because B_c = D (x) W (x) W
+// (eq. `b`) is a Kronecker product too, so is  B_c S_c = (D S) (x) (W S) (x) (W S),
+// and the Schur operator is  S = (1/nu) sum_c (B_c S_c) Lam_c^{-1} (B_c S_c)^T.
+// One CG step is therefore six passes of batched 1D line transforms (three
+// from pressure space to the scaled eigen-coefficients, three back) over all
+// three components, instead of B^T, A^{-1} (six passes) and B separately.
+//   start:  Ft_c = S_c^T F_c,  R = sum_c (B_c S_c) Lam_c^{-1} Ft_c / nu - G
+//   end:    U_c = S_c Lam_c^{-1} (Ft_c - (B_c S_c)^T P) / nu
+// Every patch tensor lives in shared memory in a (2k+3) x (2k+2) x (2k+2)
+// box (odd x stride: strided line accesses hit distinct banks).
 //
 // The same kernel, with the right-hand side set to unit vectors, builds the
 // dense pseudo-inverse of the coarse problem at setup: on a 2^3 mesh the one
@@ -29,11 +37,14 @@ namespace stk {
 template <int K>
 struct PatchCfg {
   static constexpr int ND = K + 1, NPC = 2 * K + 1, NPD = 2 * K + 2;
-  static constexpr int NV1 = NPC * NPD * NPD;  // one velocity component
+  static constexpr int NV1 = NPC * NPD * NPD;  // one velocity component (unpadded)
   static constexpr int NV = 3 * NV1;
   static constexpr int NP = NPD * NPD * NPD;
-  static constexpr int NT = (K <= 2) ? 128 : 256;
+  static constexpr int BX = NPD + 1;           // padded x extent of every patch tensor
+  static constexpr int BOX = BX * NPD * NPD;   // one padded tensor
+  static constexpr int NT = ((3 * NPD * NPD + 31) / 32) * 32;  // one thread per line of a pass
   static constexpr int NW = NT / 32;
+  static constexpr int MINB = (K == 1) ? 8 : (K == 2) ? 4 : (K == 3) ? 3 : (K == 4) ? 2 : 1;
 };
 
 template <typename T>
@@ -65,201 +76,202 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return s;
 }
 
-// Extents of velocity component c on the patch: NPC along c, NPD otherwise.
-template <int K>
-__device__ __forceinline__ int vext(int c, int d) {
-  return (c == d) ? PatchCfg<K>::NPC : PatchCfg<K>::NPD;
+// two sums at once
+template <typename T, int NW>
+__device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    red[w] = a;
+    red[NW + w] = b;
+  }
+  __syncthreads();
+  a = T(0);
+  b = T(0);
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    a += red[i];
+    b += red[NW + i];
+  }
 }
 
-// Line transforms of all three velocity components along direction d.
-// forward: out_j = sum_i S[i][j] in_i  (S^T), backward: out_i = sum_j S[i][j] in_j.
-template <int K, typename T>
-__device__ void transform_dir(const T* __restrict__ in, T* __restrict__ out, int d, bool forward,
-                              const PatchTables<T>& tb, const int* type) {
+__device__ __forceinline__ int box_stride(int d, int bx, int npd) { return d == 0 ? 1 : (d == 1 ? bx : bx * npd); }
+
+// pass kinds: velocity eigen-transform (S^T: VEL_FWD, S: VEL_BWD), pressure to
+// eigen-coefficients ((B S)^T: BT), eigen-coefficients to pressure (B S: BF)
+enum { VEL_FWD = 0, VEL_BWD = 1, BT = 2, BF = 3 };
+// epilogues of a pass
+enum { EPI_NONE = 0, EPI_SCALE = 1, EPI_FT_AND_SCALE = 2, EPI_SUB_SCALE = 3 };
+
+struct PatchGeo {
+  int type[3];
+  __device__ __forceinline__ int t(int d) const { return d == 0 ? type[0] : (d == 1 ? type[1] : type[2]); }
+};
+
+// Extent of component c along direction e during a pass of kind MODE, given
+// the directions already transformed in the current chain (bit mask).
+template <int K, int MODE>
+__device__ __forceinline__ int ext_of(int c, int e, int done) {
+  using C = PatchCfg<K>;
+  const int vel = (e == c) ? C::NPC : C::NPD;
+  if (MODE == VEL_FWD || MODE == VEL_BWD) return vel;
+  const bool tr = (done >> e) & 1;
+  if (MODE == BT) return tr ? vel : C::NPD;
+  return tr ? C::NPD : vel;  // BF
+}
+
+// One pass: every line along direction d of the three component tensors.
+// in_shared: all components read the same (pressure) box.  Epilogues scale by
+// inv_nu / (lam_0 + lam_1 + lam_2) of the output node (the last pass of a
+// chain toward eigen-coefficients).
+template <int K, typename T, int MODE>
+__device__ void patch_pass(const T* __restrict__ in, T* __restrict__ out, int d, int done, bool in_shared, int epi,
+                           const T* __restrict__ Ft, T* __restrict__ out2, const PatchTables<T>& tb,
+                           const PatchGeo& g) {
   using C = PatchCfg<K>;
   constexpr int NMAX = C::NPD;
-  // lines per component: NV1 / extent along d
-  const int lines_c0 = C::NV1 / vext<K>(0, d);
-  const int lines_c1 = C::NV1 / vext<K>(1, d);
-  const int total = lines_c0 + lines_c1 + C::NV1 / vext<K>(2, d);
+  const int e1 = (d == 0) ? 1 : 0, e2 = (d == 2) ? 1 : 2;
+  int lines[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) lines[c] = ext_of<K, MODE>(c, e1, done) * ext_of<K, MODE>(c, e2, done);
+  const int total = lines[0] + lines[1] + lines[2];
+  const int sd = box_stride(d, C::BX, C::NPD);
   for (int L = threadIdx.x; L < total; L += C::NT) {
-    int c, l;
-    if (L < lines_c0) {
-      c = 0;
-      l = L;
-    } else if (L < lines_c0 + lines_c1) {
+    int c = 0, l = L;
+    if (l >= lines[0]) {
+      l -= lines[0];
       c = 1;
-      l = L - lines_c0;
-    } else {
-      c = 2;
-      l = L - lines_c0 - lines_c1;
+      if (l >= lines[1]) {
+        l -= lines[1];
+        c = 2;
+      }
     }
-    const int e0 = vext<K>(c, 0), e1 = vext<K>(c, 1);
-    const int n = vext<K>(c, d);
-    int base, stride;
-    if (d == 0) {
-      base = l * e0;
-      stride = 1;
-    } else if (d == 1) {
-      const int i0 = l % e0, i2 = l / e0;
-      base = i0 + e0 * e1 * i2;
-      stride = e0;
+    const int x1 = ext_of<K, MODE>(c, e1, done);
+    const int i1 = l % x1, i2 = l / x1;
+    const int base = i1 * box_stride(e1, C::BX, C::NPD) + i2 * box_stride(e2, C::BX, C::NPD);
+    const T* src = in + (in_shared ? 0 : c * C::BOX) + base;
+    T* dst = out + c * C::BOX + base;
+    const bool along_c = (d == c);
+    int n_in, n_out, ncol;
+    const T* M;
+    if (MODE == VEL_FWD || MODE == VEL_BWD) {
+      n_in = n_out = ncol = along_c ? C::NPC : C::NPD;
+      M = along_c ? tb.SC : tb.SD[g.t(d)];
+    } else if (MODE == BT) {
+      n_in = C::NPD;
+      n_out = ncol = along_c ? C::NPC : C::NPD;
+      M = along_c ? tb.EC : tb.FM[g.t(d)];
     } else {
-      base = l;
-      stride = e0 * e1;
+      n_in = ncol = along_c ? C::NPC : C::NPD;
+      n_out = C::NPD;
+      M = along_c ? tb.EC : tb.FM[g.t(d)];
     }
-    base += c * C::NV1;
-    const T* S = (d == c) ? tb.SC : tb.SD[type[d]];
     T v[NMAX];
 #pragma unroll
-    for (int i = 0; i < NMAX; ++i) v[i] = (i < n) ? in[base + i * stride] : T(0);
-    if (forward) {
+    for (int i = 0; i < NMAX; ++i) v[i] = (i < n_in) ? src[i * sd] : T(0);
+    // eigenvalues of the two fixed directions (scaling epilogues only)
+    T lam_fixed = T(0);
+    if (epi != EPI_NONE) {
+      const int ii[2] = {i1, i2};
+      const int ee[2] = {e1, e2};
 #pragma unroll
-      for (int j = 0; j < NMAX; ++j) {
-        if (j >= n) break;
-        T acc = T(0);
+      for (int q = 0; q < 2; ++q) lam_fixed += (ee[q] == c) ? tb.LC[ii[q]] : tb.LD[g.t(ee[q])][ii[q]];
+    }
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+      if (j >= n_out) break;
+      T acc = T(0);
+      if (MODE == VEL_FWD || MODE == BT) {
 #pragma unroll
         for (int i = 0; i < NMAX; ++i)
-          if (i < n) acc += S[i * n + j] * v[i];
-        out[base + j * stride] = acc;
+          if (i < n_in) acc += M[i * ncol + j] * v[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+          if (i < n_in) acc += M[j * ncol + i] * v[i];
       }
-    } else {
-#pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        if (i >= n) break;
-        T acc = T(0);
-#pragma unroll
-        for (int j = 0; j < NMAX; ++j)
-          if (j < n) acc += S[i * n + j] * v[j];
-        out[base + i * stride] = acc;
+      const int o = j * sd;
+      if (epi == EPI_NONE) {
+        dst[o] = acc;
+      } else {
+        const T lam = lam_fixed + (along_c ? tb.LC[j] : tb.LD[g.t(d)][j]);
+        const T inv = tb.inv_nu / lam;
+        if (epi == EPI_SCALE) {
+          dst[o] = inv * acc;
+        } else if (epi == EPI_FT_AND_SCALE) {
+          dst[o] = acc;                                   // Ft = S^T F
+          out2[c * C::BOX + base + o] = inv * acc;        // Lam^{-1} Ft / nu
+        } else {
+          dst[o] = inv * (Ft[c * C::BOX + base + o] - acc);
+        }
       }
     }
   }
   __syncthreads();
 }
 
-// Y = A^{-1} X for the three velocity components; A is scratch, X may equal Y.
-template <int K, typename T>
-__device__ void fdm_inverse(const T* X, T* Abuf, T* Y, const PatchTables<T>& tb, const int* type) {
-  using C = PatchCfg<K>;
-  transform_dir<K, T>(X, Abuf, 0, true, tb, type);
-  transform_dir<K, T>(Abuf, Y, 1, true, tb, type);
-  transform_dir<K, T>(Y, Abuf, 2, true, tb, type);
-  for (int i = threadIdx.x; i < C::NV; i += C::NT) {
-    const int c = i / C::NV1, li = i - c * C::NV1;
-    const int e0 = vext<K>(c, 0), e1 = vext<K>(c, 1);
-    const int i0 = li % e0, i1 = (li / e0) % e1, i2 = li / (e0 * e1);
-    const T l0 = (c == 0) ? tb.LC[i0] : tb.LD[type[0]][i0];
-    const T l1 = (c == 1) ? tb.LC[i1] : tb.LD[type[1]][i1];
-    const T l2 = (c == 2) ? tb.LC[i2] : tb.LD[type[2]][i2];
-    Abuf[i] *= tb.inv_nu / (l0 + l1 + l2);
-  }
-  __syncthreads();
-  transform_dir<K, T>(Abuf, Y, 2, false, tb, type);
-  transform_dir<K, T>(Y, Abuf, 1, false, tb, type);
-  transform_dir<K, T>(Abuf, Y, 0, false, tb, type);
-}
-
-// Gout = B V (pressure nodes)
-template <int K, typename T>
-__device__ void apply_B(const T* V, T* Gout, const PatchTables<T>& tb) {
-  using C = PatchCfg<K>;
-  for (int q = threadIdx.x; q < C::NP; q += C::NT) {
-    const int q0 = q % C::NPD, q1 = (q / C::NPD) % C::NPD, q2 = q / (C::NPD * C::NPD);
-    T acc = T(0);
-    {  // component x: D along x, masses along y, z
-      const T* v = V + 0 * C::NV1 + C::NPC * (q1 + C::NPD * q2);
-      T s = T(0);
-#pragma unroll
-      for (int a = 0; a < C::NPC; ++a) s += tb.DL[q0 * C::NPC + a] * v[a];
-      acc += tb.W[q1] * tb.W[q2] * s;
-    }
-    {  // component y
-      const T* v = V + 1 * C::NV1 + q0 + C::NPD * C::NPC * q2;
-      T s = T(0);
-#pragma unroll
-      for (int a = 0; a < C::NPC; ++a) s += tb.DL[q1 * C::NPC + a] * v[a * C::NPD];
-      acc += tb.W[q0] * tb.W[q2] * s;
-    }
-    {  // component z
-      const T* v = V + 2 * C::NV1 + q0 + C::NPD * q1;
-      T s = T(0);
-#pragma unroll
-      for (int a = 0; a < C::NPC; ++a) s += tb.DL[q2 * C::NPC + a] * v[a * C::NPD * C::NPD];
-      acc += tb.W[q0] * tb.W[q1] * s;
-    }
-    Gout[q] = acc;
-  }
-  __syncthreads();
-}
-
-// Vout = B^T P (velocity nodes)
-template <int K, typename T>
-__device__ void apply_BT(const T* Pin, T* Vout, const PatchTables<T>& tb) {
-  using C = PatchCfg<K>;
-  for (int i = threadIdx.x; i < C::NV; i += C::NT) {
-    const int c = i / C::NV1, li = i - c * C::NV1;
-    const int e0 = vext<K>(c, 0), e1 = vext<K>(c, 1);
-    const int i0 = li % e0, i1 = (li / e0) % e1, i2 = li / (e0 * e1);
-    const int ii[3] = {i0, i1, i2};
-    const int a = ii[c];
-    // pressure index with q_c running, others fixed
-    int pbase, pstride;
-    if (c == 0) {
-      pbase = C::NPD * (i1 + C::NPD * i2);
-      pstride = 1;
-    } else if (c == 1) {
-      pbase = i0 + C::NPD * C::NPD * i2;
-      pstride = C::NPD;
-    } else {
-      pbase = i0 + C::NPD * i1;
-      pstride = C::NPD * C::NPD;
-    }
-    T s = T(0);
-#pragma unroll
-    for (int q = 0; q < C::NPD; ++q) s += tb.DL[q * C::NPC + a] * Pin[pbase + q * pstride];
-    const int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
-    Vout[i] = tb.W[ii[d1]] * tb.W[ii[d2]] * s;
-  }
-  __syncthreads();
-}
-
-// global index of patch-local DoF j (velocity components then pressure)
+// global index of the local velocity node (c; i0, i1, i2) or pressure node (c = 3)
 template <int K>
-__device__ __forceinline__ int64_t patch_global(int j, const int* v, int m) {
-  using C = PatchCfg<K>;
-  constexpr int ND = C::ND;
+__device__ __forceinline__ int64_t patch_node_global(int c, int i0, int i1, int i2, const int* v, int m) {
+  constexpr int ND = K + 1;
   const int64_t nvel = (int64_t)(m + 1) * m * m;
-  if (j < C::NV) {
-    const int c = j / C::NV1, li = j - c * C::NV1;
-    const int e0 = vext<K>(c, 0), e1 = vext<K>(c, 1);
-    const int ii[3] = {li % e0, (li / e0) % e1, li / (e0 * e1)};
-    int64_t g[3];
-    for (int d = 0; d < 3; ++d) g[d] = (int64_t)(v[d] - 1) * ND + ii[d] + (d == c ? 1 : 0);
+  const int ii[3] = {i0, i1, i2};
+  int64_t g[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) g[d] = (int64_t)(v[d] - 1) * ND + ii[d] + (d == c ? 1 : 0);
+  if (c < 3) {
     const int64_t E0 = (c == 0) ? m + 1 : m, E1 = (c == 1) ? m + 1 : m;
     return c * nvel + g[0] + E0 * (g[1] + E1 * g[2]);
   }
-  const int q = j - C::NV;
-  const int qq[3] = {q % C::NPD, (q / C::NPD) % C::NPD, q / (C::NPD * C::NPD)};
-  int64_t g[3];
-  for (int d = 0; d < 3; ++d) g[d] = (int64_t)(v[d] - 1) * ND + qq[d];
   return 3 * nvel + g[0] + (int64_t)m * (g[1] + (int64_t)m * g[2]);
 }
 
-template <int K, typename T>
-__global__ void __launch_bounds__(PatchCfg<K>::NT) patch_kernel(PatchArgs<T> A) {
+// patch-local DoF j (velocity components then pressure, x fastest, unpadded)
+template <int K>
+__device__ __forceinline__ void patch_local_decode(int j, int& c, int& i0, int& i1, int& i2) {
   using C = PatchCfg<K>;
+  if (j < C::NV) {
+    c = j / C::NV1;
+    const int li = j - c * C::NV1;
+    const int e0 = (c == 0) ? C::NPC : C::NPD, e1 = (c == 1) ? C::NPC : C::NPD;
+    i0 = li % e0;
+    i1 = (li / e0) % e1;
+    i2 = li / (e0 * e1);
+  } else {
+    c = 3;
+    const int q = j - C::NV;
+    i0 = q % C::NPD;
+    i1 = (q / C::NPD) % C::NPD;
+    i2 = q / (C::NPD * C::NPD);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ int64_t patch_global(int j, const int* v, int m) {
+  int c, i0, i1, i2;
+  patch_local_decode<K>(j, c, i0, i1, i2);
+  return patch_node_global<K>(c, i0, i1, i2, v, m);
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(PatchCfg<K>::NT, PatchCfg<K>::MINB) patch_kernel(PatchArgs<T> A) {
+  using C = PatchCfg<K>;
+  constexpr int BX = C::BX, BOX = C::BOX, NPD = C::NPD;
   __shared__ PatchTables<T> tb;
-  __shared__ T red[C::NW];
+  __shared__ T red[2 * C::NW];
   extern __shared__ __align__(16) unsigned char patch_smem[];
-  T* Fv = reinterpret_cast<T*>(patch_smem);  // velocity rhs F, later F - B^T P
-  T* V1 = Fv + C::NV;
-  T* V2 = V1 + C::NV;
-  T* G = V2 + C::NV;
-  T* Pp = G + C::NP;
-  T* R = Pp + C::NP;
-  T* Dd = R + C::NP;
-  T* Sd = Dd + C::NP;
+  T* Ft = reinterpret_cast<T*>(patch_smem);  // 3 boxes: S^T F, kept to the end
+  T* Ba = Ft + 3 * BOX;                      // 3 boxes of work space
+  T* Bb = Ba + 3 * BOX;                      // 3 boxes of work space
+  T* Dd = Bb + 3 * BOX;                      // CG search direction (pressure box)
+  T* R = Dd + BOX;                           // CG residual
+  T* Pp = R + BOX;                           // pressure solution (holds G until it is set to 0)
+  T* SD = Pp + BOX;                          // S applied to the search direction
 
   const int tid = threadIdx.x;
   for (int i = tid; i < (int)(sizeof(PatchTables<T>) / sizeof(T)); i += C::NT)
@@ -277,84 +289,115 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT) patch_kernel(PatchArgs<T> A) 
   } else {
     v[0] = v[1] = v[2] = 1;
   }
-  int type[3];
-  for (int d = 0; d < 3; ++d) type[d] = (v[d] == 1 ? 1 : 0) | (v[d] == A.n - 1 ? 2 : 0);
+  PatchGeo g;
+  for (int d = 0; d < 3; ++d) g.type[d] = (v[d] == 1 ? 1 : 0) | (v[d] == A.n - 1 ? 2 : 0);
 
-  // ---- gather the local right-hand side
+  // ---- gather F (velocity boxes in Ba) and G (pressure box in Pp)
   for (int j = tid; j < C::NV + C::NP; j += C::NT) {
+    int c, i0, i1, i2;
+    patch_local_decode<K>(j, c, i0, i1, i2);
     T val;
     if (A.mode == 0)
-      val = A.r[patch_global<K>(j, v, A.m)];
+      val = A.r[patch_node_global<K>(c, i0, i1, i2, v, A.m)];
     else
       val = (j == (int)blockIdx.x) ? T(1) : T(0);
-    if (j < C::NV)
-      Fv[j] = val;
+    const int o = i0 + BX * (i1 + NPD * i2);
+    if (c < 3)
+      Ba[c * BOX + o] = val;
     else
-      G[j - C::NV] = val;
+      Pp[o] = val;
   }
   __syncthreads();
 
-  // ---- rhs of the Schur system: B A^{-1} F - G, projected to mean zero
-  fdm_inverse<K, T>(Fv, V2, V1, tb, type);  // V1 = A^{-1} F
-  apply_B<K, T>(V1, R, tb);
-  T part = T(0);
+  // ---- Ft = S^T F; Bb = Lam^{-1} Ft / nu
+  patch_pass<K, T, VEL_FWD>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_FWD>(Bb, Ba, 1, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_FWD>(Ba, Ft, 2, 0, false, EPI_FT_AND_SCALE, nullptr, Bb, tb, g);
+  // ---- R = sum_c (B_c S_c) Bb_c - G
+  patch_pass<K, T, BF>(Bb, Ba, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BF>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BF>(Bb, Ba, 2, 3, false, EPI_NONE, nullptr, nullptr, tb, g);
+  T s1 = T(0), s2 = T(0);
   for (int q = tid; q < C::NP; q += C::NT) {
-    R[q] -= G[q];
-    part += R[q];
+    const int o = (q % NPD) + BX * (q / NPD);
+    const T r = (Ba[o] + Ba[BOX + o] + Ba[2 * BOX + o]) - Pp[o];
+    R[o] = r;
+    s1 += r;
   }
-  T mean = block_sum<T, C::NW>(part, red) / T(C::NP);
-  part = T(0);
+  T mean = block_sum<T, C::NW>(s1, red) / T(C::NP);
+  s2 = T(0);
   for (int q = tid; q < C::NP; q += C::NT) {
-    const T rv = R[q] - mean;
-    R[q] = rv;
-    Dd[q] = rv;
-    Pp[q] = T(0);
-    part += rv * rv;
+    const int o = (q % NPD) + BX * (q / NPD);
+    const T r = R[o] - mean;
+    R[o] = r;
+    Dd[o] = r;
+    Pp[o] = T(0);
+    s2 += r * r;
   }
-  T rr = block_sum<T, C::NW>(part, red);
+  T rr = block_sum<T, C::NW>(s2, red);
   const T rr0 = rr;
-  // ---- conjugate gradients on the Schur complement
+
+  // ---- conjugate gradients on the mean-free pressures
   for (int it = 0; it < A.cg_iters; ++it) {
     if (A.cg_tol_mode && rr <= A.cg_tol * A.cg_tol * rr0) break;
     if (!(rr > T(0))) break;
-    apply_BT<K, T>(Dd, V1, tb);
-    fdm_inverse<K, T>(V1, V2, V1, tb, type);
-    apply_B<K, T>(V1, Sd, tb);
-    part = T(0);
-    for (int q = tid; q < C::NP; q += C::NT) part += Dd[q] * Sd[q];
+    patch_pass<K, T, BT>(Dd, Ba, 0, 0, true, EPI_NONE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BT>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BT>(Bb, Ba, 2, 3, false, EPI_SCALE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BF>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BF>(Bb, Ba, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BF>(Ba, Bb, 2, 3, false, EPI_NONE, nullptr, nullptr, tb, g);
+    T part = T(0);
+    for (int q = tid; q < C::NP; q += C::NT) {
+      const int o = (q % NPD) + BX * (q / NPD);
+      const T s = Bb[o] + Bb[BOX + o] + Bb[2 * BOX + o];
+      SD[o] = s;
+      part += Dd[o] * s;
+    }
     const T dSd = block_sum<T, C::NW>(part, red);
     if (!(dSd > T(0))) break;
     const T alpha = rr / dSd;
-    part = T(0);
+    s1 = T(0);
+    s2 = T(0);
     for (int q = tid; q < C::NP; q += C::NT) {
-      Pp[q] += alpha * Dd[q];
-      const T rv = R[q] - alpha * Sd[q];
-      R[q] = rv;
-      part += rv;
+      const int o = (q % NPD) + BX * (q / NPD);
+      Pp[o] += alpha * Dd[o];
+      const T r = R[o] - alpha * SD[o];
+      R[o] = r;
+      s1 += r;
+      s2 += r * r;
     }
-    mean = block_sum<T, C::NW>(part, red) / T(C::NP);
-    part = T(0);
-    for (int q = tid; q < C::NP; q += C::NT) {
-      const T rv = R[q] - mean;
-      R[q] = rv;
-      part += rv * rv;
-    }
-    const T rr_new = block_sum<T, C::NW>(part, red);
+    block_sum2<T, C::NW>(s1, s2, red);
+    mean = s1 / T(C::NP);
+    T rr_new = s2 - s1 * mean;  // sum (r - mean)^2
+    if (rr_new < T(0)) rr_new = T(0);
     const T beta = rr_new / rr;
-    for (int q = tid; q < C::NP; q += C::NT) Dd[q] = R[q] + beta * Dd[q];
+    for (int q = tid; q < C::NP; q += C::NT) {
+      const int o = (q % NPD) + BX * (q / NPD);
+      const T r = R[o] - mean;
+      R[o] = r;
+      Dd[o] = r + beta * Dd[o];
+    }
     rr = rr_new;
     __syncthreads();
   }
-  // ---- velocity: U = A^{-1} (F - B^T P)
-  apply_BT<K, T>(Pp, V1, tb);
-  for (int i = tid; i < C::NV; i += C::NT) Fv[i] -= V1[i];
-  __syncthreads();
-  fdm_inverse<K, T>(Fv, V2, V1, tb, type);  // V1 = U
+
+  // ---- U_c = S_c Lam_c^{-1} (Ft_c - (B_c S_c)^T P) / nu
+  patch_pass<K, T, BT>(Pp, Ba, 0, 0, true, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BT>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BT>(Bb, Ba, 2, 3, false, EPI_SUB_SCALE, Ft, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD>(Bb, Ba, 1, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD>(Ba, Bb, 2, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+
   // ---- scatter
   for (int j = tid; j < C::NV + C::NP; j += C::NT) {
-    const T val = (j < C::NV) ? V1[j] : Pp[j - C::NV];
+    int c, i0, i1, i2;
+    patch_local_decode<K>(j, c, i0, i1, i2);
+    const int o = i0 + BX * (i1 + NPD * i2);
+    const T val = (c < 3) ? Bb[c * BOX + o] : Pp[o];
     if (A.mode == 0)
-      A.x[patch_global<K>(j, v, A.m)] += val;
+      A.x[patch_node_global<K>(c, i0, i1, i2, v, A.m)] += val;
     else
       A.cols[(int64_t)blockIdx.x * (C::NV + C::NP) + j] = (double)val;
   }
@@ -363,7 +406,7 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT) patch_kernel(PatchArgs<T> A) 
 template <int K>
 size_t patch_smem_bytes(size_t esize) {
   using C = PatchCfg<K>;
-  return esize * (3 * C::NV + 5 * C::NP);
+  return esize * (9 * C::BOX + 4 * C::BOX);
 }
 
 template <int K, typename T>
@@ -379,7 +422,6 @@ static cudaError_t launch_patch_k(PatchArgs<T> a, int nblocks, cudaStream_t s) {
   if (nblocks > 0) patch_kernel<K, T><<<nblocks, C::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
-
 template <typename T>
 static cudaError_t dispatch_patch(int k, PatchArgs<T> a, int nblocks, cudaStream_t s) {
   switch (k) {
