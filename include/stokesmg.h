@@ -67,6 +67,8 @@ typedef struct stk_options {
   double local_cg_tol;   /* relative CG residual in TOL mode, default 1e-8              */
   double penalty_factor; /* gamma = penalty_factor (k+1)(k+2)/h, default 1             */
   void* stream;          /* cudaStream_t used by every call, NULL = default stream     */
+  int use_graphs;        /* 1 (default): stk_solve replays its V-cycle as a captured
+                            CUDA graph (needs a non-NULL stream); 0: direct launches */
 } stk_options;
 
 typedef struct stk_problem stk_problem;
@@ -164,6 +166,21 @@ int stk_vcycle(stk_problem* P, int dtype, const void* b, void* x);
  * STK_ENOCONV (x holds the last iterate, info filled) when max_iter is reached
  * first.  The first call allocates the Krylov basis (2 restart + 1 vectors). */
 int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info);
+
+/* Solve `count` independent problems (each with its own setup, mesh, degree
+ * and options) to ||b_i - A_i x_i|| <= rtol ||b_i||, by the same method as
+ * stk_solve.  The host interleaves the solves: every round it enqueues one
+ * step of each unfinished solve on that problem's stream, then waits for each
+ * stream and advances its Krylov state, so problems on distinct non-NULL
+ * streams run concurrently on the GPU (many small problems fill the GPU that
+ * one alone cannot; the mixed-precision V-cycles replay captured CUDA
+ * graphs).  b[i], x[i]: FP64 device vectors of problem i's finest level.
+ * infos may be NULL, else count entries.  Synchronous.  Returns STK_OK,
+ * STK_ENOCONV if any solve reached its max_iter, or the first other error;
+ * stk_last_error(NULL) names the failing problem.  No problem may appear
+ * twice. */
+int stk_solve_batch(stk_problem* const* problems, int count, const double* const* b, double* const* x, double rtol,
+                    stk_solve_info* infos);
 
 /* b = right-hand side of a manufactured problem on the finest level
  * (Sec. 3.3): velocity rows (f, phi_i) with f = -nu Laplace(u) + grad p and

@@ -11,7 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "F64", "F32"]
+__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "solve_batch", "F64", "F32"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBNAME = "libstokesmg.so"
@@ -38,6 +38,7 @@ class Options(ctypes.Structure):
         ("local_cg_tol", ctypes.c_double),
         ("penalty_factor", ctypes.c_double),
         ("stream", ctypes.c_void_p),
+        ("use_graphs", ctypes.c_int),
     ]
 
 
@@ -88,6 +89,7 @@ def load_library():
         "stk_solve": (ctypes.c_int, [P, P, P, ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_rhs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P]),
         "stk_smooth_static": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
+        "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -113,7 +115,7 @@ class StokesMG:
 
     def __init__(self, n: int, k: int, nu: float = 1.0, *, precision: int = PREC_FP64, gmres_restart: int = 20,
                  max_iter: int = 200, local_cg_mode: int = CG_FIXED, local_cg_iters: int = 15,
-                 local_cg_tol: float = 1e-8, penalty_factor: float = 1.0, stream=None):
+                 local_cg_tol: float = 1e-8, penalty_factor: float = 1.0, use_graphs: bool = True, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -125,6 +127,7 @@ class StokesMG:
         opt.precision, opt.gmres_restart, opt.max_iter = precision, gmres_restart, max_iter
         opt.local_cg_mode, opt.local_cg_iters, opt.local_cg_tol = local_cg_mode, local_cg_iters, local_cg_tol
         opt.penalty_factor = penalty_factor
+        opt.use_graphs = 1 if use_graphs else 0
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         opt.stream = ctypes.c_void_p(s.cuda_stream)
@@ -269,3 +272,27 @@ class StokesMG:
         n = info.iterations
         return {"iterations": n, "converged": bool(info.converged), "relres": info.relres, "nu": info.nu,
                 "seconds": info.seconds, "residuals": list(info.residuals[: min(n, 255) + 1]), "status": rc}
+
+
+def solve_batch(problems, bs, xs, rtol: float = 1e-8):
+    """Solve several independent problems together (stk_solve_batch); returns a list of info dicts.
+
+    For concurrency each problem should have been created with its own CUDA stream.
+    """
+    lib = load_library()
+    n = len(problems)
+    P = ctypes.c_void_p
+    hs = (P * n)(*[p.h for p in problems])
+    bp = (P * n)(*[p._vec(b, p.num_levels - 1, F64) for p, b in zip(problems, bs)])
+    xp = (P * n)(*[p._vec(x, p.num_levels - 1, F64) for p, x in zip(problems, xs)])
+    infos = (SolveInfo * n)()
+    rc = lib.stk_solve_batch(hs, n, bp, xp, float(rtol), infos)
+    if rc != 0 and rc != -4:
+        raise StokesError(rc, lib.stk_last_error(None).decode())
+    out = []
+    for i in range(n):
+        it = infos[i].iterations
+        out.append({"iterations": it, "converged": bool(infos[i].converged), "relres": infos[i].relres,
+                    "nu": infos[i].nu, "seconds": infos[i].seconds,
+                    "residuals": list(infos[i].residuals[: min(it, 255) + 1])})
+    return out

@@ -63,8 +63,10 @@ void free_problem(stk_problem* P) {
   if (P->xfer32) cudaFree(P->xfer32);
   if (P->pmean_w) cudaFree(P->pmean_w);
   if (P->coarse_inv) cudaFree(P->coarse_inv);
-  if (P->mixed_b) cudaFree(P->mixed_b);
-  if (P->mixed_x) cudaFree(P->mixed_x);
+  for (double* c : P->coarse3)
+    if (c) cudaFree(c);
+  for (int d = 0; d < 2; ++d)
+    if (P->mg[d].graph) cudaGraphExecDestroy(P->mg[d].graph);
   delete P;
 }
 
@@ -74,8 +76,8 @@ int check_dtype(stk_problem* P, int dtype) {
 }
 
 int check_mg(stk_problem* P) {
-  if (P->levels[0].n != 2)
-    return fail(P, STK_ESTATE, "the V-cycle needs a hierarchy that coarsens to 2 cells per side (n = 2^L)");
+  if (P->levels[0].n != 2 && P->levels[0].n != 3)
+    return fail(P, STK_ESTATE, "the V-cycle needs a hierarchy that coarsens to 2 or 3 cells per side");
   return STK_OK;
 }
 
@@ -99,6 +101,7 @@ int stk_default_options(stk_options* opt) {
   opt->local_cg_tol = 1e-8;
   opt->penalty_factor = 1.0;
   opt->stream = nullptr;
+  opt->use_graphs = 1;
   return STK_OK;
 }
 
@@ -303,6 +306,27 @@ int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve
   std::string err;
   rc = stk::run_solve(P, b, x, rtol, info, err);
   if (rc) return fail(P, rc, err);
+  return STK_OK;
+}
+
+int stk_solve_batch(stk_problem* const* problems, int count, const double* const* b, double* const* x, double rtol,
+                    stk_solve_info* infos) {
+  if (!problems || count < 1 || !b || !x) return fail(nullptr, STK_EINVAL, "solve_batch: empty or NULL arguments");
+  if (!(rtol > 0.0)) return fail(nullptr, STK_EINVAL, "rtol must be positive");
+  for (int i = 0; i < count; ++i) {
+    stk_problem* P = problems[i];
+    if (!P) return fail(nullptr, STK_EINVAL, "solve_batch: NULL problem");
+    int rc;
+    if ((rc = check_mg(P)) || (rc = check_vec(P, b[i], "b")) || (rc = check_vec(P, x[i], "x"))) {
+      g_setup_error = "problem " + std::to_string(i) + ": " + P->err;
+      return rc;
+    }
+    for (int j = 0; j < i; ++j)
+      if (problems[j] == P) return fail(nullptr, STK_EINVAL, "solve_batch: a problem appears twice");
+  }
+  std::string err;
+  const int rc = stk::run_solve_batch(problems, count, b, x, rtol, infos, err);
+  if (rc) return fail(nullptr, rc, err);
   return STK_OK;
 }
 

@@ -83,6 +83,71 @@ __device__ __forceinline__ void stage_layers(T* __restrict__ U, const T* __restr
   }
 }
 
+// Element e of the staged layers 1..K+1 of a cell: (a, jj, ll) in global
+// memory order (x fastest) so that loads coalesce.
+template <int K>
+__device__ __forceinline__ void stage_decode(int e, int c, int& a, int& jj, int& ll) {
+  using Cfg = ApplyCfg<K>;
+  constexpr int ND = Cfg::ND, J = Cfg::J;
+  if (c == 0) {
+    a = e % ND;
+    const int r = e / ND;
+    jj = r % J;
+    ll = r / J;
+  } else if (c == 1) {
+    jj = e % J;
+    const int r = e / J;
+    a = r % ND;
+    ll = r / ND;
+  } else {
+    jj = e % J;
+    const int r = e / J;
+    ll = r % J;
+    a = r / J;
+  }
+  a += 1;
+}
+
+// Load layers 1..K+1 of cell cc into registers (corners and out-of-domain: 0).
+template <int K, typename T, int NREG>
+__device__ __forceinline__ void stage_fetch(T* regs, const T* __restrict__ u, int c, int cc, int j0, int l0, int m,
+                                            int64_t sc, int64_t s1, int64_t s2) {
+  using Cfg = ApplyCfg<K>;
+  constexpr int ND = Cfg::ND, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
+  constexpr int total = ND * J * J;
+#pragma unroll
+  for (int i = 0; i < NREG; ++i) {
+    const int e = threadIdx.x + i * NT;
+    T v = T(0);
+    if (e < total) {
+      int a, jj, ll;
+      stage_decode<K>(e, c, a, jj, ll);
+      const bool hj = (jj < H) || (jj >= H + TJ), hl = (ll < H) || (ll >= H + TJ);
+      const int gj = j0 - H + jj, gl = l0 - H + ll, ic = cc * ND + a;
+      if (!(hj && hl) && gj >= 0 && gj < m && gl >= 0 && gl < m && ic > 0 && ic < m)
+        v = u[ic * sc + gj * s1 + gl * s2];
+    }
+    regs[i] = v;
+  }
+}
+
+template <int K, typename T, int NREG>
+__device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, int c) {
+  using Cfg = ApplyCfg<K>;
+  constexpr int ND = Cfg::ND, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
+  constexpr int total = ND * J * J;
+#pragma unroll
+  for (int i = 0; i < NREG; ++i) {
+    const int e = threadIdx.x + i * NT;
+    if (e < total) {
+      int a, jj, ll;
+      stage_decode<K>(e, c, a, jj, ll);
+      const bool hj = (jj < H) || (jj >= H + TJ), hl = (ll < H) || (ll >= H + TJ);
+      if (!(hj && hl)) U[(a * J + ll) * J + jj] = regs[i];
+    }
+  }
+}
+
 template <int K, typename T>
 __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyArgs<T> A) {
   using Cfg = ApplyCfg<K>;
@@ -133,18 +198,46 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
   __syncthreads();
   const T sj = tab.S[bj], sl = tab.S[bl], ss = sj * sl;
 
-  for (int cc = (cc0 > 0 ? cc0 - 1 : 0); cc < cc1; ++cc) {
+  // Software pipeline (FP32): the layers, pressure values and b entries of the
+  // next cell are fetched into registers while the current cell is computed.
+  // FP64 is bound by the FP64 pipe and stages synchronously (fewer registers).
+  constexpr bool PIPE = sizeof(T) == 4 && K <= 3;
+  constexpr int NREG = PIPE ? (ND * J * J + NT - 1) / NT : 1;
+  T nxt[NREG];
+  T pv_next[ND], b_next[ND];
+  const int cstart = (cc0 > 0 ? cc0 - 1 : 0);
+  // the first step of a CTA computes its bottom node; later steps carry it
+  stage_layers<K, T, NC>(U, u, 0, c, cstart, j0, l0, m, sc, s1, s2);
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      pv_next[q] = p[(int64_t)(cstart * ND + q) * psc + pline_off];
+      b_next[q] = bc ? bc[(int64_t)(cstart * ND + q) * sc + line_off] : T(0);
+    }
+  }
+  __syncthreads();
+  for (int cc = cstart; cc < cc1; ++cc) {
     const bool warm = cc < cc0;  // carry-only step for the cell below the chunk
-    // the first step of a CTA computes the bottom node; later steps carry it
-    const int a0 = (cc == (cc0 > 0 ? cc0 - 1 : 0)) ? 0 : 1;
-    // ---- stage layers a0..K+1 of u_c (with one cell of halo in d1 and d2)
-    if (a0 == 0)
-      stage_layers<K, T, NC>(U, u, 0, c, cc, j0, l0, m, sc, s1, s2);
-    else
-      stage_layers<K, T, ND>(U, u, 1, c, cc, j0, l0, m, sc, s1, s2);
-    __syncthreads();
+    const int a0 = (cc == cstart) ? 0 : 1;
+    T pv[ND], bv[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      pv[q] = ss * pv_next[q];
+      bv[q] = b_next[q];
+    }
+    const bool has_next = cc + 1 < cc1;
+    if (has_next) {
+      if constexpr (PIPE) stage_fetch<K, T, NREG>(nxt, u, c, cc + 1, j0, l0, m, sc, s1, s2);
+      if (active) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) {
+          pv_next[q] = p[(int64_t)((cc + 1) * ND + q) * psc + pline_off];
+          b_next[q] = bc ? bc[(int64_t)((cc + 1) * ND + q) * sc + line_off] : T(0);
+        }
+      }
+    }
     if (active) {
-      T tv[NC], uv[NC], pv[ND], z[NC];
+      T tv[NC], uv[NC], z[NC];
       tv[0] = tcar;
       uv[0] = ucar;
 #pragma unroll
@@ -170,8 +263,6 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
         uv[a] = ss * U[(a * J + tl + H) * J + tj + H];
       }
 #pragma unroll
-      for (int q = 0; q < ND; ++q) pv[q] = ss * p[(int64_t)(cc * ND + q) * psc + pline_off];
-#pragma unroll
       for (int i = 0; i < NC; ++i) {
         T acc = T(0);
 #pragma unroll
@@ -186,7 +277,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
           const int ic = cc * ND + i;
           const int64_t g = (int64_t)ic * sc + line_off;
           T val = (i == 0) ? z[0] + zcar : z[i];
-          val = A.alpha * val + (bc ? bc[g] : T(0));
+          val = A.alpha * val + bv[i];
           yc[g] = (ic == 0) ? T(0) : val;
         }
         if (cc == n - 1) yc[(int64_t)m * sc + line_off] = T(0);
@@ -196,6 +287,13 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
       zcar = z[NC - 1];
     }
     __syncthreads();
+    if (has_next) {
+      if constexpr (PIPE)
+        stage_put<K, T, NREG>(U, nxt, c);
+      else
+        stage_layers<K, T, ND>(U, u, 1, c, cc + 1, j0, l0, m, sc, s1, s2);
+      __syncthreads();
+    }
   }
 }
 

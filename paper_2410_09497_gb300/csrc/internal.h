@@ -58,16 +58,19 @@ constexpr int kMaxPD = 2 * kMaxDegree + 2;  // patch nodes, discontinuous direct
 //   W[j]      diagonal patch mass of a discontinuous direction
 //   EC[q][j]  = sum_a DL[q][a] SC[a][j]: the divergence factor in the eigenbasis
 //   FM[t][q][j] = W[q] SD[t][q][j]: the mass factor in the eigenbasis
+// The four transform matrices are stored with rows of kRowStride entries
+// (zero padded, 16-byte aligned) so that kernels read a row with vector loads.
+constexpr int kRowStride = 12;
 template <typename T>
 struct PatchTables {
-  T SC[kMaxPC * kMaxPC];
+  alignas(16) T SC[kMaxPC * kRowStride];
+  alignas(16) T SD[4][kMaxPD * kRowStride];
+  alignas(16) T EC[kMaxPD * kRowStride];
+  alignas(16) T FM[4][kMaxPD * kRowStride];
   T LC[kMaxPC];
-  T SD[4][kMaxPD * kMaxPD];
   T LD[4][kMaxPD];
   T DL[kMaxPD * kMaxPC];
   T W[kMaxPD];
-  T EC[kMaxPD * kMaxPC];
-  T FM[4][kMaxPD * kMaxPD];
   T inv_nu;
 };
 
@@ -109,7 +112,9 @@ struct Level {
 
 struct MgWork {
   bool ready = false;
-  std::vector<void*> r, b, x;  // per level: residual, coarse rhs, coarse solution
+  std::vector<void*> r, b, x;  // per level: residual, right-hand side, solution
+  int vcycle_runs = 0;          // V-cycles run on the finest-level buffers
+  cudaGraphExec_t graph = nullptr;  // captured V-cycle on b.back() -> x.back()
 };
 
 struct KrylovWork {
@@ -133,10 +138,9 @@ struct stk_problem {
   float* xfer32 = nullptr;
   double* pmean_w = nullptr;       // device Gauss weights x h of the finest level (pressure mean)
   double* coarse_inv = nullptr;    // dense pseudo-inverse of the 2^3 coarse problem, patch order
+  double* coarse3[3] = {nullptr, nullptr, nullptr};  // FP64 b, x, r of a 3^3 coarse mesh
   stk::MgWork mg[2];               // [STK_F64], [STK_F32]
   stk::KrylovWork kry;
-  void* mixed_b = nullptr;         // FP32 copies of the finest rhs / solution (mixed precision)
-  void* mixed_x = nullptr;
   std::string err;
 };
 
@@ -152,6 +156,8 @@ cudaError_t launch_restrict(const stk_problem* P, int fine_level, int dtype, con
 // smoother.cu
 int patch_local_size(int k);
 cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x);
+cudaError_t launch_patch_colour_cg(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x,
+                                   int cg_tol_mode, int cg_iters, double cg_tol);
 cudaError_t launch_coarse_columns(const stk_problem* P, double* cols, int max_iter, double tol);
 cudaError_t launch_coarse_solve(const stk_problem* P, int dtype, const void* b, void* x);
 // solver.cu
@@ -161,6 +167,8 @@ cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void
 cudaError_t run_vcycle(stk_problem* P, int dtype, const void* b, void* x);
 cudaError_t run_coarse_solve(stk_problem* P, int dtype, const void* b, void* x);
 int run_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info, std::string& err);
+int run_solve_batch(stk_problem* const* Ps, int count, const double* const* b, double* const* x, double rtol,
+                    stk_solve_info* infos, std::string& err);
 // rhs.cu
 cudaError_t launch_rhs(const stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq,
                        const double* p_amp, double* b);

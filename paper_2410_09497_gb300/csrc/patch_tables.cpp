@@ -165,10 +165,13 @@ template <typename T>
 void fill_patch_tables(const PatchTables1D& p, PatchTables<T>* out) {
   *out = PatchTables<T>{};
   const int k = p.k, npc = 2 * k + 1, npd = 2 * k + 2;
-  for (int i = 0; i < npc * npc; ++i) out->SC[i] = (T)p.SC[i];
+  constexpr int RS = kRowStride;
+  for (int i = 0; i < npc; ++i)
+    for (int j = 0; j < npc; ++j) out->SC[i * RS + j] = (T)p.SC[i * npc + j];
   for (int i = 0; i < npc; ++i) out->LC[i] = (T)p.LC[i];
   for (int t = 0; t < 4; ++t) {
-    for (int i = 0; i < npd * npd; ++i) out->SD[t][i] = (T)p.SD[t][i];
+    for (int i = 0; i < npd; ++i)
+      for (int j = 0; j < npd; ++j) out->SD[t][i * RS + j] = (T)p.SD[t][i * npd + j];
     for (int i = 0; i < npd; ++i) out->LD[t][i] = (T)p.LD[t][i];
   }
   for (int i = 0; i < npd * npc; ++i) out->DL[i] = (T)p.DL[i];
@@ -178,11 +181,11 @@ void fill_patch_tables(const PatchTables1D& p, PatchTables<T>* out) {
     for (int j = 0; j < npc; ++j) {
       double s = 0.0;
       for (int a = 0; a < npc; ++a) s += p.DL[q * npc + a] * p.SC[a * npc + j];
-      out->EC[q * npc + j] = (T)s;
+      out->EC[q * RS + j] = (T)s;
     }
   for (int t = 0; t < 4; ++t)
     for (int q = 0; q < npd; ++q)
-      for (int j = 0; j < npd; ++j) out->FM[t][q * npd + j] = (T)(p.W[q] * p.SD[t][q * npd + j]);
+      for (int j = 0; j < npd; ++j) out->FM[t][q * RS + j] = (T)(p.W[q] * p.SD[t][q * npd + j]);
   out->inv_nu = (T)(1.0 / p.nu);
 }
 

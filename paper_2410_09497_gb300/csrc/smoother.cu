@@ -102,6 +102,34 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
 
 __device__ __forceinline__ int box_stride(int d, int bx, int npd) { return d == 0 ? 1 : (d == 1 ? bx : bx * npd); }
 
+// 16-byte vector of a matrix row
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int width = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int width = 2;
+};
+__device__ __forceinline__ void vec_fma(float* r, const float4& w, float s) {
+  r[0] += w.x * s;
+  r[1] += w.y * s;
+  r[2] += w.z * s;
+  r[3] += w.w * s;
+}
+__device__ __forceinline__ void vec_fma(double* r, const double2& w, double s) {
+  r[0] += w.x * s;
+  r[1] += w.y * s;
+}
+__device__ __forceinline__ float vec_dot(const float4& w, const float* v) {
+  return w.x * v[0] + w.y * v[1] + w.z * v[2] + w.w * v[3];
+}
+__device__ __forceinline__ double vec_dot(const double2& w, const double* v) { return w.x * v[0] + w.y * v[1]; }
+
 // pass kinds: velocity eigen-transform (S^T: VEL_FWD, S: VEL_BWD), pressure to
 // eigen-coefficients ((B S)^T: BT), eigen-coefficients to pressure (B S: BF)
 enum { VEL_FWD = 0, VEL_BWD = 1, BT = 2, BF = 3 };
@@ -130,9 +158,9 @@ __device__ __forceinline__ int ext_of(int c, int e, int done) {
 // inv_nu / (lam_0 + lam_1 + lam_2) of the output node (the last pass of a
 // chain toward eigen-coefficients).
 template <int K, typename T, int MODE>
-__device__ void patch_pass(const T* __restrict__ in, T* __restrict__ out, int d, int done, bool in_shared, int epi,
-                           const T* __restrict__ Ft, T* __restrict__ out2, const PatchTables<T>& tb,
-                           const PatchGeo& g) {
+__device__ void patch_pass_fma(const T* __restrict__ in, T* __restrict__ out, int d, int done, bool in_shared,
+                               int epi, const T* __restrict__ Ft, T* __restrict__ out2, const PatchTables<T>& tb,
+                               const PatchGeo& g) {
   using C = PatchCfg<K>;
   constexpr int NMAX = C::NPD;
   const int e1 = (d == 0) ? 1 : 0, e2 = (d == 2) ? 1 : 2;
@@ -157,23 +185,26 @@ __device__ void patch_pass(const T* __restrict__ in, T* __restrict__ out, int d,
     const T* src = in + (in_shared ? 0 : c * C::BOX) + base;
     T* dst = out + c * C::BOX + base;
     const bool along_c = (d == c);
-    int n_in, n_out, ncol;
-    const T* M;
+    int n_in, n_out;
+    const T* M;  // rows of kRowStride entries, zero padded
     if (MODE == VEL_FWD || MODE == VEL_BWD) {
-      n_in = n_out = ncol = along_c ? C::NPC : C::NPD;
+      n_in = n_out = along_c ? C::NPC : C::NPD;
       M = along_c ? tb.SC : tb.SD[g.t(d)];
     } else if (MODE == BT) {
       n_in = C::NPD;
-      n_out = ncol = along_c ? C::NPC : C::NPD;
+      n_out = along_c ? C::NPC : C::NPD;
       M = along_c ? tb.EC : tb.FM[g.t(d)];
     } else {
-      n_in = ncol = along_c ? C::NPC : C::NPD;
+      n_in = along_c ? C::NPC : C::NPD;
       n_out = C::NPD;
       M = along_c ? tb.EC : tb.FM[g.t(d)];
     }
-    T v[NMAX];
+    using V = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::width;
+    constexpr int NP4 = ((NMAX + VW - 1) / VW) * VW;  // padded row length read per row
+    T v[NP4];
 #pragma unroll
-    for (int i = 0; i < NMAX; ++i) v[i] = (i < n_in) ? src[i * sd] : T(0);
+    for (int i = 0; i < NP4; ++i) v[i] = (i < n_in) ? src[i * sd] : T(0);
     // eigenvalues of the two fixed directions (scaling epilogues only)
     T lam_fixed = T(0);
     if (epi != EPI_NONE) {
@@ -182,19 +213,38 @@ __device__ void patch_pass(const T* __restrict__ in, T* __restrict__ out, int d,
 #pragma unroll
       for (int q = 0; q < 2; ++q) lam_fixed += (ee[q] == c) ? tb.LC[ii[q]] : tb.LD[g.t(ee[q])][ii[q]];
     }
+    T res[NP4];
+    if (MODE == VEL_FWD || MODE == BT) {
+      // out_j = sum_i M[i][j] v_i: one vector load feeds VW outputs
+#pragma unroll
+      for (int j = 0; j < NP4; ++j) res[j] = T(0);
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) {
+        if (i >= n_in) break;
+        const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
+#pragma unroll
+        for (int q = 0; q < NP4 / VW; ++q) {
+          const V w = row[q];
+          vec_fma(res + q * VW, w, v[i]);
+        }
+      }
+    } else {
+      // out_i = sum_j M[i][j] v_j
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) {
+        res[i] = T(0);
+        if (i >= n_out) continue;
+        const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NP4 / VW; ++q) acc += vec_dot(row[q], v + q * VW);
+        res[i] = acc;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < NMAX; ++j) {
       if (j >= n_out) break;
-      T acc = T(0);
-      if (MODE == VEL_FWD || MODE == BT) {
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-          if (i < n_in) acc += M[i * ncol + j] * v[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-          if (i < n_in) acc += M[j * ncol + i] * v[i];
-      }
+      const T acc = res[j];
       const int o = j * sd;
       if (epi == EPI_NONE) {
         dst[o] = acc;
@@ -213,6 +263,12 @@ __device__ void patch_pass(const T* __restrict__ in, T* __restrict__ out, int d,
     }
   }
   __syncthreads();
+}
+
+template <int K, typename T, int MODE>
+__device__ __forceinline__ void patch_pass(const T* in, T* out, int d, int done, bool in_shared, int epi, const T* Ft,
+                                           T* out2, const PatchTables<T>& tb, const PatchGeo& g) {
+  patch_pass_fma<K, T, MODE>(in, out, d, done, in_shared, epi, Ft, out2, tb, g);
 }
 
 // global index of the local velocity node (c; i0, i1, i2) or pressure node (c = 3)
@@ -451,7 +507,8 @@ static void fill_common(const stk_problem* P, const Level& L, PatchArgs<T>& a) {
   a.cols = nullptr;
 }
 
-cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x) {
+cudaError_t launch_patch_colour_cg(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x,
+                                   int cg_tol_mode, int cg_iters, double cg_tol) {
   const Level& L = P->levels[level];
   int cnt[3];
   colour_counts(L.n, colour, cnt);
@@ -465,6 +522,9 @@ cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int 
     a.colour = colour;
     for (int d = 0; d < 3; ++d) a.cnt[d] = cnt[d];
     a.mode = 0;
+    a.cg_tol_mode = cg_tol_mode;
+    a.cg_iters = cg_iters;
+    a.cg_tol = cg_tol;
     return dispatch_patch<double>(P->k, a, nb, P->stream);
   }
   PatchArgs<float> a;
@@ -475,7 +535,15 @@ cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int 
   a.colour = colour;
   for (int d = 0; d < 3; ++d) a.cnt[d] = cnt[d];
   a.mode = 0;
+  a.cg_tol_mode = cg_tol_mode;
+  a.cg_iters = cg_iters;
+  a.cg_tol = (float)cg_tol;
   return dispatch_patch<float>(P->k, a, nb, P->stream);
+}
+
+cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x) {
+  return launch_patch_colour_cg(P, level, dtype, colour, r, x, P->opt.local_cg_mode == STK_CG_TOL,
+                                P->opt.local_cg_iters, P->opt.local_cg_tol);
 }
 
 int patch_local_size(int k) {

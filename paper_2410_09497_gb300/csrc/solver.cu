@@ -165,6 +165,16 @@ cudaError_t ensure_mg_workspace(stk_problem* P, int dtype) {
 }
 
 cudaError_t ensure_coarse(stk_problem* P) {
+  if (P->levels[0].n != 2) {
+    // 3^3 coarse mesh: FP64 vectors for the coarse sweeps
+    if (P->coarse3[0]) return cudaSuccess;
+    const size_t bytes = sizeof(double) * (size_t)P->levels[0].ntotal;
+    for (int i = 0; i < 3; ++i) {
+      cudaError_t e = cudaMalloc(&P->coarse3[i], bytes);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   if (P->coarse_inv) return cudaSuccess;
   const int NL = patch_local_size(P->k);
   cudaError_t e = cudaMalloc(&P->coarse_inv, sizeof(double) * (size_t)NL * NL);
@@ -189,9 +199,45 @@ cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void
   return cudaSuccess;
 }
 
+// Coarse solve P_0^{-1} (Sec. 3).  On the 2^3 mesh: the dense FP64
+// pseudo-inverse.  On a 3^3 mesh (n = 3 * 2^L) the problem has eight
+// overlapping vertex patches, one per colour; the solve is kCoarseSweeps
+// steps of the multiplicative Schwarz iteration in FP64 with local solves
+// converged to 1e-13, from x = 0.
+constexpr int kCoarseSweeps = 24;
+
+template <typename S, typename D>
+__global__ void copy_convert_kernel(const S* __restrict__ src, D* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (D)src[i];
+}
+
+static cudaError_t coarse_level_solve(stk_problem* P, int dtype, const void* b, void* x) {
+  if (P->levels[0].n == 2) return launch_coarse_solve(P, dtype, b, x);
+  const int64_t n = P->levels[0].ntotal;
+  double *cb = P->coarse3[0], *cx = P->coarse3[1], *cr = P->coarse3[2];
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  if (dtype == STK_F64)
+    copy_convert_kernel<double, double><<<grid, 256, 0, P->stream>>>((const double*)b, cb, n);
+  else
+    copy_convert_kernel<float, double><<<grid, 256, 0, P->stream>>>((const float*)b, cb, n);
+  cudaError_t e = cudaMemsetAsync(cx, 0, sizeof(double) * n, P->stream);
+  for (int s = 0; e == cudaSuccess && s < kCoarseSweeps; ++s)
+    for (int colour = 0; e == cudaSuccess && colour < 8; ++colour) {
+      e = launch_apply(P, 0, STK_F64, cx, cb, cr, -1.0);
+      if (e == cudaSuccess) e = launch_patch_colour_cg(P, 0, STK_F64, colour, cr, cx, 1, 500, 1e-13);
+    }
+  if (e != cudaSuccess) return e;
+  if (dtype == STK_F64)
+    copy_convert_kernel<double, double><<<grid, 256, 0, P->stream>>>(cx, (double*)x, n);
+  else
+    copy_convert_kernel<double, float><<<grid, 256, 0, P->stream>>>(cx, (float*)x, n);
+  return cudaGetLastError();
+}
+
 static cudaError_t vcycle_rec(stk_problem* P, int level, int dtype, const void* b, void* x) {
   cudaError_t e;
-  if (level == 0) return launch_coarse_solve(P, dtype, b, x);
+  if (level == 0) return coarse_level_solve(P, dtype, b, x);
   const size_t es = dtype == STK_F64 ? 8 : 4;
   MgWork& W = P->mg[dtype];
   e = cudaMemsetAsync(x, 0, (size_t)P->levels[level].ntotal * es, P->stream);
@@ -214,7 +260,7 @@ cudaError_t run_vcycle(stk_problem* P, int dtype, const void* b, void* x) {
 cudaError_t run_coarse_solve(stk_problem* P, int dtype, const void* b, void* x) {
   cudaError_t e = ensure_coarse(P);
   if (e != cudaSuccess) return e;
-  return launch_coarse_solve(P, dtype, b, x);
+  return coarse_level_solve(P, dtype, b, x);
 }
 
 // -------------------------------------------------------------------- FGMRES
@@ -240,21 +286,51 @@ static cudaError_t dots(stk_problem* P, const double* V, int nv, const double* w
   return cudaGetLastError();
 }
 
+// One V-cycle on the finest-level buffers of the workspace (fixed pointers):
+// the first call runs it directly (setting kernel attributes and building the
+// coarse pseudo-inverse), the second captures it into a CUDA graph, later
+// calls replay the graph.  Graphs need a non-default stream and opt.use_graphs.
+static cudaError_t fixed_vcycle(stk_problem* P, int dtype) {
+  const int L = (int)P->levels.size() - 1;
+  MgWork& W = P->mg[dtype];
+  const bool graphs = P->opt.use_graphs && P->stream != nullptr;
+  if (!graphs || W.vcycle_runs == 0) {
+    ++W.vcycle_runs;
+    return run_vcycle(P, dtype, W.b[L], W.x[L]);
+  }
+  if (!W.graph) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e1 = vcycle_rec(P, L, dtype, W.b[L], W.x[L]);
+    e = cudaStreamEndCapture(P->stream, &g);
+    if (e1 != cudaSuccess) e = e1;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&W.graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      W.graph = nullptr;
+      return e;
+    }
+  }
+  return cudaGraphLaunch(W.graph, P->stream);
+}
+
 static cudaError_t precondition(stk_problem* P, const double* v, double* z) {
   const int L = (int)P->levels.size() - 1;
   const int64_t n = P->levels[L].ntotal;
   if (P->opt.precision == STK_PREC_MIXED) {
-    cudaError_t e = ensure_mg_workspace(P, STK_F32);
+    MgWork& W = P->mg[STK_F32];
+    convert_kernel<double, float><<<grid_for(n), 256, 0, P->stream>>>(v, (float*)W.b[L], n);
+    cudaError_t e = fixed_vcycle(P, STK_F32);
     if (e != cudaSuccess) return e;
-    float* b32 = (float*)P->mixed_b;
-    float* x32 = (float*)P->mixed_x;
-    convert_kernel<double, float><<<grid_for(n), 256, 0, P->stream>>>(v, b32, n);
-    e = run_vcycle(P, STK_F32, b32, x32);
-    if (e != cudaSuccess) return e;
-    convert_kernel<float, double><<<grid_for(n), 256, 0, P->stream>>>(x32, z, n);
+    convert_kernel<float, double><<<grid_for(n), 256, 0, P->stream>>>((const float*)W.x[L], z, n);
     return cudaGetLastError();
   }
-  return run_vcycle(P, STK_F64, v, z);
+  MgWork& W = P->mg[STK_F64];
+  cudaError_t e = cudaMemcpyAsync(W.b[L], v, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream);
+  if (e == cudaSuccess) e = fixed_vcycle(P, STK_F64);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(z, W.x[L], sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream);
+  return e;
 }
 
 cudaError_t project_pressure_mean(stk_problem* P, double* x) {
@@ -265,128 +341,256 @@ cudaError_t project_pressure_mean(stk_problem* P, double* x) {
   return cudaGetLastError();
 }
 
-int run_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info, std::string& err) {
-  auto t0 = std::chrono::steady_clock::now();
-  const int m = P->opt.gmres_restart;
-  const int L = (int)P->levels.size() - 1;
-  const int64_t n = P->levels[L].ntotal;
-  cudaStream_t s = P->stream;
-  cudaError_t e = ensure_krylov(P);
-  if (e == cudaSuccess && P->opt.precision == STK_PREC_MIXED && !P->mixed_b) {
-    e = cudaMalloc(&P->mixed_b, sizeof(float) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&P->mixed_x, sizeof(float) * n);
-  }
-  if (e == cudaSuccess) e = ensure_mg_workspace(P, P->opt.precision == STK_PREC_MIXED ? STK_F32 : STK_F64);
-  if (e == cudaSuccess) e = ensure_coarse(P);
-  if (e != cudaSuccess) {
-    err = std::string("solve setup: ") + cudaGetErrorString(e);
-    return e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA;
-  }
-  KrylovWork& K = P->kry;
+// dst = src * s (host scalar)
+__global__ void scale_by_kernel(const double* __restrict__ src, double* __restrict__ dst, double s, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e] * s;
+}
+
+// Flexible GMRES(restart) as a resumable state machine: issue() enqueues the
+// GPU work of the current phase on the problem's stream and ends with a copy
+// of the scalars the host needs; complete() runs after the stream is idle and
+// decides the next phase.  stk_solve drives one machine; stk_solve_batch
+// interleaves many, one stream each, so their kernels overlap on the GPU.
+struct SolveMachine {
+  enum Phase { START, ITER, CYCLE_END, FINISH, DONE };
+  stk_problem* P = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double rtol = 0;
+  stk_solve_info* info = nullptr;
   stk_solve_info local{};
-  stk_solve_info& I = info ? *info : local;
-  std::memset(&I, 0, sizeof(I));
-  I.residuals[0] = 1.0;
-  // ||b||
-  dots(P, b, 1, b, n, K.h, 0);
-  cudaMemcpyAsync(K.h_host, K.h, sizeof(double), cudaMemcpyDeviceToHost, s);
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
-    err = std::string("solve: ") + cudaGetErrorString(e);
-    return STK_ECUDA;
+  Phase phase = START;
+  int status = STK_OK;
+  std::string err;
+  double bnorm = 0, beta = 0, hn_prev = 1.0;
+  int its = 0, j = 0, jdone = 0;
+  bool converged = false, need_normalize = false;
+  std::vector<double> H, cs, sn, g;
+  std::chrono::steady_clock::time_point t0;
+
+  stk_solve_info& I() { return info ? *info : local; }
+  int m() const { return P->opt.gmres_restart; }
+  int64_t n() const { return P->levels.back().ntotal; }
+  cudaStream_t s() const { return P->stream; }
+
+  int prepare() {
+    t0 = std::chrono::steady_clock::now();
+    cudaError_t e = ensure_krylov(P);
+    if (e == cudaSuccess) e = ensure_mg_workspace(P, P->opt.precision == STK_PREC_MIXED ? STK_F32 : STK_F64);
+    if (e == cudaSuccess) e = ensure_coarse(P);
+    if (e != cudaSuccess) return fail_cuda(e, "solve setup");
+    std::memset(&I(), 0, sizeof(stk_solve_info));
+    I().residuals[0] = 1.0;
+    H.assign((m() + 1) * m(), 0.0);
+    cs.assign(m(), 0.0);
+    sn.assign(m(), 0.0);
+    g.assign(m() + 1, 0.0);
+    return STK_OK;
   }
-  const double bnorm = std::sqrt(K.h_host[0]);
-  cudaMemsetAsync(x, 0, sizeof(double) * n, s);
-  int its = 0;
-  bool converged = bnorm == 0.0;
-  double beta = bnorm;
-  // r0 = b (x0 = 0) into V_0 after scaling
-  const double* rsrc = b;
-  double* rtmp = K.V + (size_t)m * n;  // the last basis slot doubles as residual storage
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1);
-  while (!converged && its < P->opt.max_iter) {
-    // V_0 = r / beta
-    K.h_host[0] = beta;
-    cudaMemcpyAsync(K.h, K.h_host, sizeof(double), cudaMemcpyHostToDevice, s);
-    scale_kernel<<<grid_for(n), 256, 0, s>>>(rsrc, K.V, K.h, n);
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int jdone = 0;
-    for (int j = 0; j < m; ++j) {
-      double* Vj = K.V + (size_t)j * n;
-      double* Zj = K.Z + (size_t)j * n;
-      double* w = K.V + (size_t)(j + 1) * n;
-      if ((e = precondition(P, Vj, Zj)) != cudaSuccess) break;
-      if ((e = launch_apply(P, L, STK_F64, Zj, nullptr, w, 1.0)) != cudaSuccess) break;
-      // two passes of classical Gram-Schmidt
-      dots(P, K.V, j + 1, w, n, K.h, 0);
-      multi_axpy_kernel<<<grid_for(n), 256, 0, s>>>(w, K.V, j + 1, K.h, n);
-      dots(P, K.V, j + 1, w, n, K.h + kMaxBasis, 0);
-      multi_axpy_kernel<<<grid_for(n), 256, 0, s>>>(w, K.V, j + 1, K.h + kMaxBasis, n);
-      dots(P, w, 1, w, n, K.h + kMaxBasis + j + 1, 0);
-      cudaMemcpyAsync(K.h_host, K.h, sizeof(double) * 2 * kMaxBasis, cudaMemcpyDeviceToHost, s);
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
-      for (int i = 0; i <= j; ++i) H[i * m + j] = K.h_host[i] + K.h_host[kMaxBasis + i];
-      const double hn = std::sqrt(K.h_host[kMaxBasis + j + 1]);
-      H[(j + 1) * m + j] = hn;
-      K.h_host[0] = hn;
-      cudaMemcpyAsync(K.h, K.h_host, sizeof(double), cudaMemcpyHostToDevice, s);
-      scale_kernel<<<grid_for(n), 256, 0, s>>>(w, w, K.h, n);
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-        H[i * m + j] = t;
+
+  int fail_cuda(cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    status = e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA;
+    phase = DONE;
+    return status;
+  }
+
+  // enqueue the work of the current phase
+  int issue() {
+    KrylovWork& K = P->kry;
+    const int64_t N = n();
+    cudaError_t e = cudaSuccess;
+    switch (phase) {
+      case START:
+        e = dots(P, b, 1, b, N, K.h, 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(double) * N, s());
+        break;
+      case ITER: {
+        double* Vj = K.V + (size_t)j * N;
+        double* Zj = K.Z + (size_t)j * N;
+        double* w = K.V + (size_t)(j + 1) * N;
+        if (j == 0) {
+          // V_0 = r / beta (r = b when x0 = 0, else the last true residual in V_m)
+          const double* r = (its == 0) ? b : K.V + (size_t)m() * N;
+          scale_by_kernel<<<grid_for(N), 256, 0, s()>>>(r, K.V, 1.0 / beta, N);
+        } else if (need_normalize) {
+          scale_by_kernel<<<grid_for(N), 256, 0, s()>>>(Vj, Vj, 1.0 / hn_prev, N);
+        }
+        e = precondition(P, Vj, Zj);
+        if (e == cudaSuccess) e = launch_apply(P, (int)P->levels.size() - 1, STK_F64, Zj, nullptr, w, 1.0);
+        if (e != cudaSuccess) break;
+        // two passes of classical Gram-Schmidt
+        dots(P, K.V, j + 1, w, N, K.h, 0);
+        multi_axpy_kernel<<<grid_for(N), 256, 0, s()>>>(w, K.V, j + 1, K.h, N);
+        dots(P, K.V, j + 1, w, N, K.h + kMaxBasis, 0);
+        multi_axpy_kernel<<<grid_for(N), 256, 0, s()>>>(w, K.V, j + 1, K.h + kMaxBasis, N);
+        e = dots(P, w, 1, w, N, K.h + kMaxBasis + j + 1, 0);
+        break;
       }
-      const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
-      cs[j] = H[j * m + j] / den;
-      sn[j] = H[(j + 1) * m + j] / den;
-      H[j * m + j] = den;
-      H[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++its;
-      jdone = j + 1;
-      if (its < 256) I.residuals[its] = std::fabs(g[j + 1]) / bnorm;
-      if (std::fabs(g[j + 1]) <= rtol * bnorm || its >= P->opt.max_iter) break;
+      case CYCLE_END: {
+        // y = H^{-1} g (upper triangular), x += Z y, true residual into V_m
+        Coeffs c{};
+        const int mm = m();
+        for (int i = jdone - 1; i >= 0; --i) {
+          double sum = g[i];
+          for (int l = i + 1; l < jdone; ++l) sum -= H[i * mm + l] * c.y[l];
+          c.y[i] = sum / H[i * mm + i];
+        }
+        update_x_kernel<<<grid_for(N), 256, 0, s()>>>(x, K.Z, jdone, c, N);
+        double* rtmp = K.V + (size_t)mm * N;
+        e = launch_apply(P, (int)P->levels.size() - 1, STK_F64, x, b, rtmp, -1.0);
+        if (e == cudaSuccess) e = dots(P, rtmp, 1, rtmp, N, K.h, 0);
+        break;
+      }
+      case FINISH:
+        e = project_pressure_mean(P, x);
+        break;
+      case DONE:
+        return status;
     }
-    if (e != cudaSuccess) break;
-    // y = H^{-1} g (upper triangular), x += Z y
-    Coeffs c{};
-    for (int i = jdone - 1; i >= 0; --i) {
-      double sum = g[i];
-      for (int l = i + 1; l < jdone; ++l) sum -= H[i * m + l] * c.y[l];
-      c.y[i] = sum / H[i * m + i];
+    if (e == cudaSuccess && phase != FINISH)
+      e = cudaMemcpyAsync(K.h_host, K.h, sizeof(double) * 2 * kMaxBasis, cudaMemcpyDeviceToHost, s());
+    if (e != cudaSuccess) return fail_cuda(e, "solve");
+    return STK_OK;
+  }
+
+  // host side of the current phase, after the stream has finished
+  void complete() {
+    KrylovWork& K = P->kry;
+    const int mm = m();
+    switch (phase) {
+      case START:
+        bnorm = std::sqrt(K.h_host[0]);
+        beta = bnorm;
+        converged = bnorm == 0.0;
+        j = 0;
+        phase = converged ? FINISH : ITER;
+        break;
+      case ITER: {
+        for (int i = 0; i <= j; ++i) H[i * mm + j] = K.h_host[i] + K.h_host[kMaxBasis + i];
+        const double hn = std::sqrt(K.h_host[kMaxBasis + j + 1]);
+        H[(j + 1) * mm + j] = hn;
+        hn_prev = hn;
+        need_normalize = true;
+        if (j == 0) std::fill(g.begin(), g.end(), 0.0), g[0] = beta;
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * H[i * mm + j] + sn[i] * H[(i + 1) * mm + j];
+          H[(i + 1) * mm + j] = -sn[i] * H[i * mm + j] + cs[i] * H[(i + 1) * mm + j];
+          H[i * mm + j] = t;
+        }
+        const double den = std::hypot(H[j * mm + j], H[(j + 1) * mm + j]);
+        cs[j] = H[j * mm + j] / den;
+        sn[j] = H[(j + 1) * mm + j] / den;
+        H[j * mm + j] = den;
+        H[(j + 1) * mm + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++its;
+        jdone = j + 1;
+        if (its < 256) I().residuals[its] = std::fabs(g[j + 1]) / bnorm;
+        if (std::fabs(g[j + 1]) <= rtol * bnorm || its >= P->opt.max_iter || j + 1 == mm)
+          phase = CYCLE_END;
+        else
+          ++j;
+        break;
+      }
+      case CYCLE_END:
+        beta = std::sqrt(K.h_host[0]);
+        converged = beta <= rtol * bnorm;
+        if (converged || its >= P->opt.max_iter) {
+          phase = FINISH;
+        } else {
+          j = 0;
+          need_normalize = false;
+          std::fill(H.begin(), H.end(), 0.0);
+          phase = ITER;
+        }
+        break;
+      case FINISH: {
+        stk_solve_info& In = I();
+        In.iterations = its;
+        In.converged = converged ? 1 : 0;
+        In.relres = bnorm > 0 ? beta / bnorm : 0.0;
+        const double last = its > 0 && its < 256 ? In.residuals[its] : In.relres;
+        In.nu = (its > 0 && last > 0) ? -8.0 / std::log10(std::pow(last, 1.0 / its)) : 0.0;
+        In.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (!converged) {
+          err = "GMRES reached max_iter before the tolerance";
+          status = STK_ENOCONV;
+        }
+        phase = DONE;
+        break;
+      }
+      case DONE:
+        break;
     }
-    update_x_kernel<<<grid_for(n), 256, 0, s>>>(x, K.Z, jdone, c, n);
-    // true residual
-    if ((e = launch_apply(P, L, STK_F64, x, b, rtmp, -1.0)) != cudaSuccess) break;
-    dots(P, rtmp, 1, rtmp, n, K.h, 0);
-    cudaMemcpyAsync(K.h_host, K.h, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
-    beta = std::sqrt(K.h_host[0]);
-    rsrc = rtmp;
-    converged = beta <= rtol * bnorm;
   }
-  if (e != cudaSuccess) {
-    err = std::string("solve: ") + cudaGetErrorString(e);
-    return STK_ECUDA;
+};
+
+int run_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info, std::string& err) {
+  SolveMachine M;
+  M.P = P;
+  M.b = b;
+  M.x = x;
+  M.rtol = rtol;
+  M.info = info;
+  if (M.prepare() != STK_OK) {
+    err = M.err;
+    return M.status;
   }
-  if ((e = project_pressure_mean(P, x)) == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    err = std::string("solve: ") + cudaGetErrorString(e);
-    return STK_ECUDA;
+  while (M.phase != SolveMachine::DONE) {
+    if (M.issue() != STK_OK) break;
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) {
+      M.fail_cuda(e, "solve");
+      break;
+    }
+    M.complete();
   }
-  I.iterations = its;
-  I.converged = converged ? 1 : 0;
-  I.relres = bnorm > 0 ? beta / bnorm : 0.0;
-  const double last = its > 0 && its < 256 ? I.residuals[its] : I.relres;
-  I.nu = (its > 0 && last > 0) ? -8.0 / std::log10(std::pow(last, 1.0 / its)) : 0.0;
-  I.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (!converged) {
-    err = "GMRES reached max_iter before the tolerance";
-    return STK_ENOCONV;
+  err = M.err;
+  return M.status;
+}
+
+int run_solve_batch(stk_problem* const* Ps, int count, const double* const* b, double* const* x, double rtol,
+                    stk_solve_info* infos, std::string& err) {
+  std::vector<SolveMachine> M(count);
+  for (int i = 0; i < count; ++i) {
+    M[i].P = Ps[i];
+    M[i].b = b[i];
+    M[i].x = x[i];
+    M[i].rtol = rtol;
+    M[i].info = infos ? &infos[i] : nullptr;
+    if (M[i].prepare() != STK_OK) {
+      err = "problem " + std::to_string(i) + ": " + M[i].err;
+      return M[i].status;
+    }
   }
-  return STK_OK;
+  // every round issues one phase of each unfinished solve, then completes them
+  int active = count;
+  while (active > 0) {
+    for (auto& m : M)
+      if (m.phase != SolveMachine::DONE) m.issue();
+    active = 0;
+    for (int i = 0; i < count; ++i) {
+      SolveMachine& m = M[i];
+      if (m.phase == SolveMachine::DONE) continue;
+      cudaError_t e = cudaStreamSynchronize(m.s());
+      if (e != cudaSuccess) {
+        m.fail_cuda(e, "solve");
+        continue;
+      }
+      m.complete();
+      if (m.phase != SolveMachine::DONE) ++active;
+    }
+  }
+  int worst = STK_OK;
+  for (int i = 0; i < count; ++i)
+    if (M[i].status != STK_OK && (worst == STK_OK || M[i].status != STK_ENOCONV)) {
+      worst = M[i].status;
+      err = "problem " + std::to_string(i) + ": " + M[i].err;
+    }
+  return worst;
 }
 
 }  // namespace stk

@@ -156,3 +156,35 @@ def test_rhs_matches_oracle(stk, n, k, nu):
     P.rhs(coef, b)
     assert relerr(b.cpu().numpy(), ref) <= 1e-12
     P.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_coarse_solve_on_3cube(stk, k):
+    """n = 3 * 2^L hierarchies end on a 3^3 mesh, solved by converged Schwarz sweeps."""
+    H = Hierarchy(3, k)
+    d = H.levels[0].disc
+    b = random_vector(1300 + k, d.N) * d.free_mask()
+    ref = H.coarse_solve(b)
+    P = stk.StokesMG(3, k)
+    x = dev(np.full(d.N, np.nan))
+    P.coarse_solve(dev(b), x)
+    assert relerr(x.cpu().numpy(), ref) <= 1e-9
+    P.close()
+
+
+@pytest.mark.parametrize("n,k", [(6, 2), (12, 1)])
+def test_vcycle_and_solve_on_3cube_hierarchy(stk, n, k):
+    man = Manufactured(manufactured_coefficients(5))
+    H = Hierarchy(n, k, local=("schur", 15))
+    d = H.levels[-1].disc
+    b = rhs(d, man)
+    ref = H.vcycle(b)
+    P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
+    x = dev(np.full(d.N, np.nan))
+    P.vcycle(dev(b), x)
+    assert relerr(x.cpu().numpy(), ref) <= 1e-8
+    xs = dev(np.zeros(d.N))
+    info = P.solve(dev(b), xs, rtol=1e-8)
+    _, info_ref = H.solve(b, tol=1e-8)
+    assert info["converged"] and abs(info["iterations"] - info_ref["iterations"]) <= 1
+    P.close()
