@@ -213,6 +213,49 @@ def run_solve_pair(args, stream, ws):
     return out
 
 
+def run_batch(args):
+    """Batched uneven solves: seeded sides from {8, 12, 16, 24, 32} and degrees from
+    {2, 3, 4}, mixed precision, FGMRES + graph-captured V-cycle to 1e-8 each, one
+    stream per problem; total DoF/s of stk_solve_batch against a sequential loop."""
+    import torch
+
+    from paper_2410_09497_gb300 import PREC_MIXED, StokesMG, solve_batch
+    from seeded_inputs import manufactured_coefficients, splitmix64_stream
+
+    z = splitmix64_stream(4000, 2 * args.batch)
+    sides = [8, 12, 16, 24, 32]
+    cfg = [(sides[int(z[2 * i]) % 5], 2 + int(z[2 * i + 1]) % 3) for i in range(args.batch)]
+    probs, bs, xs = [], [], []
+    for i, (n, k) in enumerate(cfg):
+        s = torch.cuda.Stream()
+        P = StokesMG(n, k, precision=PREC_MIXED, stream=s)
+        b = torch.empty(P.layout()["n_total"], dtype=torch.float64, device="cuda")
+        P.rhs(manufactured_coefficients(4000 + i), b)
+        probs.append(P)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    total = sum(p.layout()["n_total"] for p in probs)
+    for P, b, x in zip(probs, bs, xs):  # warm-up: workspace, coarse solvers, graphs
+        P.solve(b, x, 1e-8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for P, b, x in zip(probs, bs, xs):
+        P.solve(b, x, 1e-8)
+    torch.cuda.synchronize()
+    tseq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    infos = solve_batch(probs, bs, xs, 1e-8)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    for P in probs:
+        P.close()
+    return {"workload": f"{args.batch} independent manufactured Stokes solves, sides in {{8,12,16,24,32}}, k in {{2,3,4}}, mixed precision, to 1e-8",
+            "problems": cfg, "total_dofs": total, "unit": "MDoF/s", "value": total / tb / 1e6,
+            "sequential_value": total / tseq / 1e6, "batch_seconds": tb, "sequential_seconds": tseq,
+            "speedup": tseq / tb, "all_converged": all(i["converged"] for i in infos),
+            "iterations": [i["iterations"] for i in infos]}
+
+
 def run_reference(args):
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -345,6 +388,8 @@ def run_ours(args):
     }
     if args.solve_n > 0:
         line["solve"] = run_solve_pair(args, stream, ws)
+    if args.batch > 0:
+        line["batch"] = run_batch(args)
     if rank == 0 and not args.no_cpu_baseline:
         rate, info = oracle_spmv_rate(8, k, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
@@ -374,6 +419,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-n", type=int, default=64, help="mesh of the mixed-vs-FP64 solve sub-benchmark (0: skip)")
     ap.add_argument("--solve-k", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=0, help="also run N batched uneven solves (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -182,6 +182,17 @@ int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve
 int stk_solve_batch(stk_problem* const* problems, int count, const double* const* b, double* const* x, double rtol,
                     stk_solve_info* infos);
 
+/* Autotuner (no counterpart in the paper): for every level, time the operator
+ * apply in `dtype` with each candidate march length of its velocity kernel
+ * (cells per CTA: n, n/2, ..., 2) on the problem's stream and keep the
+ * fastest; every later apply, residual, smoothing step and solve of that dtype
+ * uses it.  Synchronous; allocates and frees two vectors per level. */
+int stk_autotune(stk_problem* P, int dtype);
+
+/* The march length chosen by stk_autotune for a level and dtype (0 = not
+ * tuned: the built-in choice is used). */
+int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_cta);
+
 /* b = right-hand side of a manufactured problem on the finest level
  * (Sec. 3.3): velocity rows (f, phi_i) with f = -nu Laplace(u) + grad p and
  * u = curl(psi), by the (k+3)-point Gauss rule of every cell; pressure rows

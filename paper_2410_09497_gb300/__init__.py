@@ -89,6 +89,8 @@ def load_library():
         "stk_solve": (ctypes.c_int, [P, P, P, ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_rhs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P]),
         "stk_smooth_static": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
+        "stk_autotune": (ctypes.c_int, [P, ctypes.c_int]),
+        "stk_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
     }
     for name, (res, args) in sig.items():
@@ -231,6 +233,16 @@ class StokesMG:
         dt = self._dt(x)
         self._check(self.lib.stk_smooth_static(self.h, level, dt, self._vec(x, level), self._vec(b, level, dt)))
         return x
+
+    def autotune(self, dtype: int = F32):
+        """Time the apply's march length per level for dtype and keep the fastest; returns {level: cells_per_cta}."""
+        self._check(self.lib.stk_autotune(self.h, int(dtype)))
+        out = {}
+        for level in range(self.num_levels):
+            v = ctypes.c_int()
+            self._check(self.lib.stk_tuning(self.h, level, int(dtype), ctypes.byref(v)))
+            out[level] = v.value
+        return out
 
     def coarse_solve(self, b, x):
         """x = A_0^+ b on level 0."""

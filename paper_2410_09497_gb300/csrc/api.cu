@@ -155,6 +155,8 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
     stk::CellTables<float> h32;
     stk::fill_cell_tables(L.t1d, &h64);
     stk::fill_cell_tables(L.t1d, &h32);
+    L.htab64 = h64;
+    L.htab32 = h32;
     const stk::PatchTables1D pt = stk::build_patch_tables(L.t1d);
     stk::PatchTables<double> p64;
     stk::PatchTables<float> p32;
@@ -327,6 +329,53 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
   std::string err;
   const int rc = stk::run_solve_batch(problems, count, b, x, rtol, infos, err);
   if (rc) return fail(nullptr, rc, err);
+  return STK_OK;
+}
+
+int stk_autotune(stk_problem* P, int dtype) {
+  if (!P) return STK_EINVAL;
+  int rc = check_dtype(P, dtype);
+  if (rc) return rc;
+  const size_t es = dtype == STK_F64 ? 8 : 4;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (size_t l = 0; e == cudaSuccess && l < P->levels.size(); ++l) {
+    stk::Level& L = P->levels[l];
+    void *x = nullptr, *y = nullptr;
+    e = cudaMalloc(&x, L.ntotal * es);
+    if (e == cudaSuccess) e = cudaMalloc(&y, L.ntotal * es);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, L.ntotal * es, P->stream);
+    float best = 1e30f;
+    int best_chunk = 0;
+    // candidate march lengths: the whole column down to 2 cells per CTA
+    for (int chunk = L.n; e == cudaSuccess && chunk >= 2; chunk /= 2) {
+      L.apply_chunk[dtype] = chunk;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = stk::launch_apply(P, (int)l, dtype, x, nullptr, y, 1.0);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+      for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) e = stk::launch_apply(P, (int)l, dtype, x, nullptr, y, 1.0);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_chunk = chunk;
+      }
+    }
+    L.apply_chunk[dtype] = best_chunk;
+    if (x) cudaFree(x);
+    if (y) cudaFree(y);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return status_of(P, e, "autotune");
+}
+
+int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_cta) {
+  if (!P || !cells_per_cta || level < 0 || level >= (int)P->levels.size() || (dtype != STK_F64 && dtype != STK_F32))
+    return STK_EINVAL;
+  *cells_per_cta = P->levels[level].apply_chunk[dtype];
   return STK_OK;
 }
 

@@ -31,7 +31,7 @@ struct ApplyArgs {
   const T* b;  // optional: y = alpha A x + b
   T* y;
   T alpha;
-  const CellTables<T>* tab;
+  CellTables<T> tv;  // by value: constant-bank operands for compile-time indices
   int n, m;
   int chunk, nchunks, ntile;
 };
@@ -149,7 +149,7 @@ __device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, int 
 }
 
 template <int K, typename T>
-__global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyArgs<T> A) {
+__global__ void __launch_bounds__(ApplyCfg<K>::NT, (sizeof(T) == 4 && K <= 3 ? 2 : 1)) apply_velocity_kernel(ApplyArgs<T> A) {
   using Cfg = ApplyCfg<K>;
   constexpr int ND = Cfg::ND, NC = Cfg::NC, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
   __shared__ CellTables<T> tab;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
   const T* bc = A.b ? A.b + c * nvel : nullptr;
 
   for (int i = tid; i < (int)(sizeof(CellTables<T>) / sizeof(T)); i += NT)
-    reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(A.tab)[i];
+    reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(&A.tv)[i];
 
   const int cj = jn / ND, bj = jn - cj * ND, cl = ln / ND, bl = ln - cl * ND;
   const int typej = (cj == 0) ? 1 : ((cj == n - 1) ? 2 : 0);
@@ -197,6 +197,19 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
   T tcar = T(0), ucar = T(0), zcar = T(0);
   __syncthreads();
   const T sj = tab.S[bj], sl = tab.S[bl], ss = sj * sl;
+  // FP32: the 1D penalty rows of this thread's two discontinuous nodes live in
+  // registers for the whole march (FP64 reads them from shared memory).
+  constexpr bool ROWREG = sizeof(T) == 4;
+  T r1s[ND], r1lo[ND], r1hi[ND], r2s[ND], r2lo[ND], r2hi[ND];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    r1s[q] = ROWREG ? tab.LS[typej][bj * ND + q] : T(0);
+    r1lo[q] = ROWREG ? tab.LLO[bj * ND + q] : T(0);
+    r1hi[q] = ROWREG ? tab.LHI[bj * ND + q] : T(0);
+    r2s[q] = ROWREG ? tab.LS[typel][bl * ND + q] : T(0);
+    r2lo[q] = ROWREG ? tab.LLO[bl * ND + q] : T(0);
+    r2hi[q] = ROWREG ? tab.LHI[bl * ND + q] : T(0);
+  }
 
   // Software pipeline (FP32): the layers, pressure values and b entries of the
   // next cell are fetched into registers while the current cell is computed.
@@ -248,16 +261,16 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
         T acc1 = T(0), acc2 = T(0);
 #pragma unroll
         for (int q = 0; q < ND; ++q) {
-          acc1 += tab.LS[typej][bj * ND + q] * row[bj0 + q];
-          acc1 += tab.LLO[bj * ND + q] * row[bj0 - ND + q];
-          acc1 += tab.LHI[bj * ND + q] * row[bj0 + ND + q];
+          acc1 += (ROWREG ? r1s[q] : tab.LS[typej][bj * ND + q]) * row[bj0 + q];
+          acc1 += (ROWREG ? r1lo[q] : tab.LLO[bj * ND + q]) * row[bj0 - ND + q];
+          acc1 += (ROWREG ? r1hi[q] : tab.LHI[bj * ND + q]) * row[bj0 + ND + q];
         }
         const int bl0 = tl - bl + H;
 #pragma unroll
         for (int q = 0; q < ND; ++q) {
-          acc2 += tab.LS[typel][bl * ND + q] * U[(a * J + bl0 + q) * J + tj + H];
-          acc2 += tab.LLO[bl * ND + q] * U[(a * J + bl0 - ND + q) * J + tj + H];
-          acc2 += tab.LHI[bl * ND + q] * U[(a * J + bl0 + ND + q) * J + tj + H];
+          acc2 += (ROWREG ? r2s[q] : tab.LS[typel][bl * ND + q]) * U[(a * J + bl0 + q) * J + tj + H];
+          acc2 += (ROWREG ? r2lo[q] : tab.LLO[bl * ND + q]) * U[(a * J + bl0 - ND + q) * J + tj + H];
+          acc2 += (ROWREG ? r2hi[q] : tab.LHI[bl * ND + q]) * U[(a * J + bl0 + ND + q) * J + tj + H];
         }
         tv[a] = sl * acc1 + sj * acc2;
         uv[a] = ss * U[(a * J + tl + H) * J + tj + H];
@@ -266,9 +279,9 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT) apply_velocity_kernel(ApplyAr
       for (int i = 0; i < NC; ++i) {
         T acc = T(0);
 #pragma unroll
-        for (int a = 0; a < NC; ++a) acc += tab.KC[i * NC + a] * uv[a] + tab.MC[i * NC + a] * tv[a];
+        for (int a = 0; a < NC; ++a) acc += A.tv.KC[i * NC + a] * uv[a] + A.tv.MC[i * NC + a] * tv[a];
 #pragma unroll
-        for (int q = 0; q < ND; ++q) acc += tab.D[q * NC + i] * pv[q];
+        for (int q = 0; q < ND; ++q) acc += A.tv.D[q * NC + i] * pv[q];
         z[i] = acc;
       }
       if (!warm) {
@@ -302,7 +315,7 @@ __global__ void __launch_bounds__(256) apply_pressure_kernel(ApplyArgs<T> A) {
   constexpr int ND = K + 1, NC = K + 2;
   __shared__ CellTables<T> tab;
   for (int i = threadIdx.x; i < (int)(sizeof(CellTables<T>) / sizeof(T)); i += blockDim.x)
-    reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(A.tab)[i];
+    reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(&A.tv)[i];
   __syncthreads();
   const int m = A.m;
   const int64_t mm = (int64_t)m * m, np = mm * m;
@@ -334,7 +347,7 @@ __global__ void __launch_bounds__(256) apply_pressure_kernel(ApplyArgs<T> A) {
 }
 
 template <int K, typename T>
-static cudaError_t launch_apply_k(const Level& L, const CellTables<T>* tab, const T* x, const T* b, T* y, T alpha,
+static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, const T* x, const T* b, T* y, T alpha,
                                   int stages, cudaStream_t s) {
   using Cfg = ApplyCfg<K>;
   ApplyArgs<T> a;
@@ -342,14 +355,17 @@ static cudaError_t launch_apply_k(const Level& L, const CellTables<T>* tab, cons
   a.b = b;
   a.y = y;
   a.alpha = alpha;
-  a.tab = tab;
+  a.tv = tab;
   a.n = L.n;
   a.m = L.m;
   a.ntile = (L.m + Cfg::TJ - 1) / Cfg::TJ;
   const int tiles = a.ntile * a.ntile;
+  // cells marched per CTA: tuned value if stk_autotune chose one, else enough
+  // CTAs for ~8 per SM with marches of at least 4 cells
+  const int tuned = L.apply_chunk[sizeof(T) == 8 ? STK_F64 : STK_F32];
   int nch = (1216 + 3 * tiles - 1) / (3 * tiles);
   nch = std::max(1, std::min(nch, L.n / 4 > 0 ? L.n / 4 : 1));
-  a.chunk = (L.n + nch - 1) / nch;
+  a.chunk = tuned > 0 ? std::min(tuned, L.n) : (L.n + nch - 1) / nch;
   a.nchunks = (L.n + a.chunk - 1) / a.chunk;
   dim3 grid(tiles * a.nchunks, 3);
   const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
@@ -370,7 +386,7 @@ static cudaError_t launch_apply_k(const Level& L, const CellTables<T>* tab, cons
 }
 
 template <typename T>
-static cudaError_t dispatch_apply(int k, const Level& L, const CellTables<T>* tab, const T* x, const T* b, T* y,
+static cudaError_t dispatch_apply(int k, const Level& L, const CellTables<T>& tab, const T* x, const T* b, T* y,
                                   T alpha, int stages, cudaStream_t s) {
   switch (k) {
     case 1: return launch_apply_k<1, T>(L, tab, x, b, y, alpha, stages, s);
@@ -386,9 +402,9 @@ cudaError_t launch_apply(const stk_problem* P, int level, int dtype, const void*
                          double alpha, int stages) {
   const Level& L = P->levels[level];
   if (dtype == STK_F64)
-    return dispatch_apply<double>(P->k, L, L.tab64, (const double*)x, (const double*)b, (double*)y, alpha, stages,
+    return dispatch_apply<double>(P->k, L, L.htab64, (const double*)x, (const double*)b, (double*)y, alpha, stages,
                                   P->stream);
-  return dispatch_apply<float>(P->k, L, L.tab32, (const float*)x, (const float*)b, (float*)y, (float)alpha, stages,
+  return dispatch_apply<float>(P->k, L, L.htab32, (const float*)x, (const float*)b, (float*)y, (float)alpha, stages,
                                P->stream);
 }
 

@@ -106,6 +106,9 @@ struct Level {
   Tables1D t1d;
   CellTables<double>* tab64 = nullptr;  // device
   CellTables<float>* tab32 = nullptr;   // device
+  CellTables<double> htab64{};          // host copies, passed to kernels by value
+  CellTables<float> htab32{};
+  int apply_chunk[2] = {0, 0};          // cells per CTA march of the apply ([dtype]); 0 = default
   PatchTables<double>* ptab64 = nullptr;  // device
   PatchTables<float>* ptab32 = nullptr;   // device
 };

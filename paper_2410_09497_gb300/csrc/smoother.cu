@@ -44,7 +44,14 @@ struct PatchCfg {
   static constexpr int BOX = BX * NPD * NPD;   // one padded tensor
   static constexpr int NT = ((3 * NPD * NPD + 31) / 32) * 32;  // one thread per line of a pass
   static constexpr int NW = NT / 32;
-  static constexpr int MINB = (K == 1) ? 8 : (K == 2) ? 4 : (K == 3) ? 3 : (K == 4) ? 2 : 1;
+};
+
+// Resident CTAs per SM the register budget must allow: as many as the shared
+// memory of one patch (13 padded tensors + tables) permits.
+template <int K, typename T>
+struct PatchOcc {
+  static constexpr int value = sizeof(T) == 4 ? ((K == 1) ? 16 : (K == 2) ? 8 : (K == 3) ? 5 : (K == 4) ? 3 : 2)
+                                              : ((K == 1) ? 8 : (K == 2) ? 4 : (K == 3) ? 3 : 1);
 };
 
 template <typename T>
@@ -315,7 +322,7 @@ __device__ __forceinline__ int64_t patch_global(int j, const int* v, int m) {
 }
 
 template <int K, typename T>
-__global__ void __launch_bounds__(PatchCfg<K>::NT, PatchCfg<K>::MINB) patch_kernel(PatchArgs<T> A) {
+__global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patch_kernel(PatchArgs<T> A) {
   using C = PatchCfg<K>;
   constexpr int BX = C::BX, BOX = C::BOX, NPD = C::NPD;
   __shared__ PatchTables<T> tb;

@@ -102,3 +102,24 @@ def test_full_size_sampled_rows(stk):
     ref = d.apply_rows(x, rows)
     assert np.abs(y[rows] - ref).max() <= 1e-12 * np.abs(ref).max()
     P.close()
+
+
+@pytest.mark.parametrize("dtype_name", ["f64", "f32"])
+def test_autotuned_apply_keeps_parity(stk, dtype_name):
+    import torch
+
+    n, k = 8, 2
+    d = Discretization(n, k)
+    A = d.assemble()
+    P = stk.StokesMG(n, k, 1.0)
+    dt = stk.F64 if dtype_name == "f64" else stk.F32
+    tuned = P.autotune(dt)
+    assert all(2 <= v <= P.layout(level)["n"] for level, v in tuned.items())
+    x = random_vector(4242, d.N)
+    tdt = torch.float64 if dtype_name == "f64" else torch.float32
+    xd = torch.from_numpy(x).to(tdt).cuda()
+    yd = torch.empty_like(xd)
+    P.apply(xd, yd)
+    ref = A @ (xd.cpu().double().numpy() * d.free_mask())
+    assert _relerr(yd.cpu().double().numpy(), ref) <= (1e-12 if dtype_name == "f64" else 1e-5)
+    P.close()
