@@ -108,44 +108,61 @@ __device__ __forceinline__ void stage_decode(int e, int c, int& a, int& jj, int&
   a += 1;
 }
 
-// Load layers 1..K+1 of cell cc into registers (corners and out-of-domain: 0).
-template <int K, typename T, int NREG>
-__device__ __forceinline__ void stage_fetch(T* regs, const T* __restrict__ u, int c, int cc, int j0, int l0, int m,
-                                            int64_t sc, int64_t s1, int64_t s2) {
+// Which elements of layers 1..K+1 this thread stages, worked out once per
+// CTA: the element's global offset for cell 0 (-1: never loaded: a corner or
+// outside the domain in d1 / d2), its shared-memory index (-1: not stored)
+// and whether it is the cell's top node (ic = m on the last cell: load 0).
+template <int NREG>
+struct StagePlan {
+  int goff[NREG];
+  int sidx[NREG];
+  unsigned top;
+};
+
+template <int K, int NREG>
+__device__ __forceinline__ void stage_plan(StagePlan<NREG>& pl, int c, int j0, int l0, int m, int64_t s1,
+                                           int64_t s2, int64_t sc) {
   using Cfg = ApplyCfg<K>;
   constexpr int ND = Cfg::ND, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
   constexpr int total = ND * J * J;
+  pl.top = 0u;
 #pragma unroll
   for (int i = 0; i < NREG; ++i) {
     const int e = threadIdx.x + i * NT;
-    T v = T(0);
+    pl.goff[i] = -1;
+    pl.sidx[i] = -1;
     if (e < total) {
       int a, jj, ll;
       stage_decode<K>(e, c, a, jj, ll);
       const bool hj = (jj < H) || (jj >= H + TJ), hl = (ll < H) || (ll >= H + TJ);
-      const int gj = j0 - H + jj, gl = l0 - H + ll, ic = cc * ND + a;
-      if (!(hj && hl) && gj >= 0 && gj < m && gl >= 0 && gl < m && ic > 0 && ic < m)
-        v = u[ic * sc + gj * s1 + gl * s2];
+      if (!(hj && hl)) {
+        pl.sidx[i] = (a * J + ll) * J + jj;
+        const int gj = j0 - H + jj, gl = l0 - H + ll;
+        if (gj >= 0 && gj < m && gl >= 0 && gl < m) pl.goff[i] = (int)(a * sc + gj * s1 + gl * s2);
+        if (a == ND) pl.top |= 1u << i;
+      }
     }
-    regs[i] = v;
+  }
+}
+
+// Load layers 1..K+1 of cell cc into registers (corners and out-of-domain: 0).
+template <int K, typename T, int NREG>
+__device__ __forceinline__ void stage_fetch(T* regs, const T* __restrict__ u, const StagePlan<NREG>& pl, int cc,
+                                            bool last_cell, int64_t sc) {
+  constexpr int ND = ApplyCfg<K>::ND;
+  const T* base = u + (int64_t)cc * ND * sc;
+#pragma unroll
+  for (int i = 0; i < NREG; ++i) {
+    const bool ok = pl.goff[i] >= 0 && !(last_cell && ((pl.top >> i) & 1u));
+    regs[i] = ok ? base[pl.goff[i]] : T(0);
   }
 }
 
 template <int K, typename T, int NREG>
-__device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, int c) {
-  using Cfg = ApplyCfg<K>;
-  constexpr int ND = Cfg::ND, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
-  constexpr int total = ND * J * J;
+__device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, const StagePlan<NREG>& pl) {
 #pragma unroll
-  for (int i = 0; i < NREG; ++i) {
-    const int e = threadIdx.x + i * NT;
-    if (e < total) {
-      int a, jj, ll;
-      stage_decode<K>(e, c, a, jj, ll);
-      const bool hj = (jj < H) || (jj >= H + TJ), hl = (ll < H) || (ll >= H + TJ);
-      if (!(hj && hl)) U[(a * J + ll) * J + jj] = regs[i];
-    }
-  }
+  for (int i = 0; i < NREG; ++i)
+    if (pl.sidx[i] >= 0) U[pl.sidx[i]] = regs[i];
 }
 
 template <int K, typename T>
@@ -217,6 +234,8 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (sizeof(T) == 4 && K <= 3 ? 2
   constexpr bool PIPE = sizeof(T) == 4 && K <= 3;
   constexpr int NREG = PIPE ? (ND * J * J + NT - 1) / NT : 1;
   T nxt[NREG];
+  StagePlan<NREG> plan;
+  if constexpr (PIPE) stage_plan<K, NREG>(plan, c, j0, l0, m, s1, s2, sc);
   T pv_next[ND], b_next[ND];
   const int cstart = (cc0 > 0 ? cc0 - 1 : 0);
   // the first step of a CTA computes its bottom node; later steps carry it
@@ -240,7 +259,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (sizeof(T) == 4 && K <= 3 ? 2
     }
     const bool has_next = cc + 1 < cc1;
     if (has_next) {
-      if constexpr (PIPE) stage_fetch<K, T, NREG>(nxt, u, c, cc + 1, j0, l0, m, sc, s1, s2);
+      if constexpr (PIPE) stage_fetch<K, T, NREG>(nxt, u, plan, cc + 1, cc + 1 == n - 1, sc);
       if (active) {
 #pragma unroll
         for (int q = 0; q < ND; ++q) {
@@ -302,7 +321,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (sizeof(T) == 4 && K <= 3 ? 2
     __syncthreads();
     if (has_next) {
       if constexpr (PIPE)
-        stage_put<K, T, NREG>(U, nxt, c);
+        stage_put<K, T, NREG>(U, nxt, plan);
       else
         stage_layers<K, T, ND>(U, u, 1, c, cc + 1, j0, l0, m, sc, s1, s2);
       __syncthreads();
