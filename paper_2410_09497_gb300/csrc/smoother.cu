@@ -160,96 +160,130 @@ __device__ __forceinline__ int ext_of(int c, int e, int done) {
   return tr ? C::NPD : vel;  // BF
 }
 
-// One line of a pass with compile-time sizes: NIN values in, NOUT values out,
-// M rows of kRowStride entries (forward: out_j = sum_i M[i][j] in_i,
-// backward: out_i = sum_j M[i][j] in_j), then the epilogue.
-template <typename T, bool FWD, int NIN, int NOUT>
-__device__ __forceinline__ void line_transform(const T* __restrict__ src, T* __restrict__ dst, int sd,
-                                               const T* __restrict__ M, int epi, T lam_fixed,
-                                               const T* __restrict__ lamd, T inv_nu, const T* __restrict__ Ft,
-                                               T* __restrict__ out2, int fto) {
-  using V = typename Vec16<T>::type;
-  constexpr int VW = Vec16<T>::width;
-  constexpr int NW_OUT = ((NOUT + VW - 1) / VW) * VW;
-  constexpr int NW_IN = ((NIN + VW - 1) / VW) * VW;
-  T v[NW_IN];
+// One pass: every line along direction d of the three component tensors.
+// in_shared: all components read the same (pressure) box.  Epilogues scale by
+// inv_nu / (lam_0 + lam_1 + lam_2) of the output node (the last pass of a
+// chain toward eigen-coefficients).
+template <int K, typename T, int MODE>
+__device__ void patch_pass_fma(const T* __restrict__ in, T* __restrict__ out, int d, int done, bool in_shared,
+                               int epi, const T* __restrict__ Ft, T* __restrict__ out2, const PatchTables<T>& tb,
+                               const PatchGeo& g) {
+  using C = PatchCfg<K>;
+  constexpr int NMAX = C::NPD;
+  const int e1 = (d == 0) ? 1 : 0, e2 = (d == 2) ? 1 : 2;
+  int lines[3];
 #pragma unroll
-  for (int i = 0; i < NW_IN; ++i) v[i] = (i < NIN) ? src[i * sd] : T(0);
-  T res[NW_OUT > NOUT ? NW_OUT : NOUT];
-  if constexpr (FWD) {
-#pragma unroll
-    for (int j = 0; j < NW_OUT; ++j) res[j] = T(0);
-#pragma unroll
-    for (int i = 0; i < NIN; ++i) {
-      const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
-#pragma unroll
-      for (int q = 0; q < NW_OUT / VW; ++q) vec_fma(res + q * VW, row[q], v[i]);
+  for (int c = 0; c < 3; ++c) lines[c] = ext_of<K, MODE>(c, e1, done) * ext_of<K, MODE>(c, e2, done);
+  const int total = lines[0] + lines[1] + lines[2];
+  const int sd = box_stride(d, C::BX, C::NPD);
+  for (int L = threadIdx.x; L < total; L += C::NT) {
+    int c = 0, l = L;
+    if (l >= lines[0]) {
+      l -= lines[0];
+      c = 1;
+      if (l >= lines[1]) {
+        l -= lines[1];
+        c = 2;
+      }
     }
-  } else {
-#pragma unroll
-    for (int i = 0; i < NOUT; ++i) {
-      const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
-      T acc = T(0);
-#pragma unroll
-      for (int q = 0; q < NW_IN / VW; ++q) acc += vec_dot(row[q], v + q * VW);
-      res[i] = acc;
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NOUT; ++j) {
-    const int o = j * sd;
-    if (epi == EPI_NONE) {
-      dst[o] = res[j];
+    // the extent along e1 is NPC or NPD: divide by compile-time constants
+    const int x1 = ext_of<K, MODE>(c, e1, done);
+    int i1, i2;
+    if (x1 == C::NPC) {
+      i1 = l % C::NPC;
+      i2 = l / C::NPC;
     } else {
-      const T inv = inv_nu / (lam_fixed + lamd[j]);
-      if (epi == EPI_SCALE) {
-        dst[o] = inv * res[j];
-      } else if (epi == EPI_FT_AND_SCALE) {
-        dst[o] = res[j];
-        out2[fto + o] = inv * res[j];
+      i1 = l % C::NPD;
+      i2 = l / C::NPD;
+    }
+    const int base = i1 * box_stride(e1, C::BX, C::NPD) + i2 * box_stride(e2, C::BX, C::NPD);
+    const T* src = in + (in_shared ? 0 : c * C::BOX) + base;
+    T* dst = out + c * C::BOX + base;
+    const bool along_c = (d == c);
+    int n_in, n_out;
+    const T* M;  // rows of kRowStride entries, zero padded
+    if (MODE == VEL_FWD || MODE == VEL_BWD) {
+      n_in = n_out = along_c ? C::NPC : C::NPD;
+      M = along_c ? tb.SC : tb.SD[g.t(d)];
+    } else if (MODE == BT) {
+      n_in = C::NPD;
+      n_out = along_c ? C::NPC : C::NPD;
+      M = along_c ? tb.EC : tb.FM[g.t(d)];
+    } else {
+      n_in = along_c ? C::NPC : C::NPD;
+      n_out = C::NPD;
+      M = along_c ? tb.EC : tb.FM[g.t(d)];
+    }
+    using V = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::width;
+    constexpr int NP4 = ((NMAX + VW - 1) / VW) * VW;  // padded row length read per row
+    T v[NP4];
+#pragma unroll
+    for (int i = 0; i < NP4; ++i) v[i] = (i < n_in) ? src[i * sd] : T(0);
+    // eigenvalues of the two fixed directions (scaling epilogues only)
+    T lam_fixed = T(0);
+    if (epi != EPI_NONE) {
+      const int ii[2] = {i1, i2};
+      const int ee[2] = {e1, e2};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) lam_fixed += (ee[q] == c) ? tb.LC[ii[q]] : tb.LD[g.t(ee[q])][ii[q]];
+    }
+    T res[NP4];
+    if (MODE == VEL_FWD || MODE == BT) {
+      // out_j = sum_i M[i][j] v_i: one vector load feeds VW outputs
+#pragma unroll
+      for (int j = 0; j < NP4; ++j) res[j] = T(0);
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) {
+        if (i >= n_in) break;
+        const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
+#pragma unroll
+        for (int q = 0; q < NP4 / VW; ++q) {
+          const V w = row[q];
+          vec_fma(res + q * VW, w, v[i]);
+        }
+      }
+    } else {
+      // out_i = sum_j M[i][j] v_j
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) {
+        res[i] = T(0);
+        if (i >= n_out) continue;
+        const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NP4 / VW; ++q) acc += vec_dot(row[q], v + q * VW);
+        res[i] = acc;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+      if (j >= n_out) break;
+      const T acc = res[j];
+      const int o = j * sd;
+      if (epi == EPI_NONE) {
+        dst[o] = acc;
       } else {
-        dst[o] = inv * (Ft[fto + o] - res[j]);
+        const T lam = lam_fixed + (along_c ? tb.LC[j] : tb.LD[g.t(d)][j]);
+        const T inv = tb.inv_nu / lam;
+        if (epi == EPI_SCALE) {
+          dst[o] = inv * acc;
+        } else if (epi == EPI_FT_AND_SCALE) {
+          dst[o] = acc;                                   // Ft = S^T F
+          out2[c * C::BOX + base + o] = inv * acc;        // Lam^{-1} Ft / nu
+        } else {
+          dst[o] = inv * (Ft[c * C::BOX + base + o] - acc);
+        }
       }
     }
   }
+  __syncthreads();
 }
 
-// One pass along direction D of kind MODE; DONE = directions already
-// transformed in the current chain.  Thread (c, u, v) owns the line of
-// component c at coordinates (u, v) in the two other directions, the same
-// thread for every pass (threads beyond the current extents idle).
-template <int K, typename T, int MODE, int D, int DONE>
-__device__ __forceinline__ void patch_pass(const T* __restrict__ in, T* __restrict__ out, bool in_shared, int epi,
-                                           const T* __restrict__ Ft, T* __restrict__ out2,
-                                           const PatchTables<T>& tb, const PatchGeo& g, int c, int u, int v) {
-  using C = PatchCfg<K>;
-  constexpr int E1 = (D == 0) ? 1 : 0, E2 = (D == 2) ? 1 : 2;
-  constexpr int SD = (D == 0) ? 1 : (D == 1 ? C::BX : C::BX * C::NPD);
-  constexpr int S1 = (E1 == 0) ? 1 : (E1 == 1 ? C::BX : C::BX * C::NPD);
-  constexpr int S2 = (E2 == 0) ? 1 : (E2 == 1 ? C::BX : C::BX * C::NPD);
-  constexpr bool FWD = (MODE == VEL_FWD || MODE == BT);
-  constexpr bool VEL = (MODE == VEL_FWD || MODE == VEL_BWD);
-  if (c < 3 && u < ext_of<K, MODE>(c, E1, DONE) && v < ext_of<K, MODE>(c, E2, DONE)) {
-    const int base = u * S1 + v * S2;
-    const T* src = in + (in_shared ? 0 : c * C::BOX) + base;
-    T* dst = out + c * C::BOX + base;
-    const int fto = c * C::BOX + base;
-    T lam_fixed = T(0);
-    if (epi != EPI_NONE)
-      lam_fixed = ((E1 == c) ? tb.LC[u] : tb.LD[g.t(E1)][u]) + ((E2 == c) ? tb.LC[v] : tb.LD[g.t(E2)][v]);
-    if (c == D) {
-      // along the component's continuous direction: NPC eigen / velocity nodes
-      constexpr int NIN = VEL ? C::NPC : (MODE == BT ? C::NPD : C::NPC);
-      constexpr int NOUT = VEL ? C::NPC : (MODE == BT ? C::NPC : C::NPD);
-      line_transform<T, FWD, NIN, NOUT>(src, dst, SD, VEL ? tb.SC : tb.EC, epi, lam_fixed, tb.LC, tb.inv_nu, Ft,
-                                        out2, fto);
-    } else {
-      const int t = g.t(D);
-      line_transform<T, FWD, C::NPD, C::NPD>(src, dst, SD, VEL ? tb.SD[t] : tb.FM[t], epi, lam_fixed, tb.LD[t],
-                                             tb.inv_nu, Ft, out2, fto);
-    }
-  }
-  __syncthreads();
+template <int K, typename T, int MODE>
+__device__ __forceinline__ void patch_pass(const T* in, T* out, int d, int done, bool in_shared, int epi, const T* Ft,
+                                           T* out2, const PatchTables<T>& tb, const PatchGeo& g) {
+  patch_pass_fma<K, T, MODE>(in, out, d, done, in_shared, epi, Ft, out2, tb, g);
 }
 
 // global index of the local velocity node (c; i0, i1, i2) or pressure node (c = 3)
@@ -328,8 +362,6 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   }
   PatchGeo g;
   for (int d = 0; d < 3; ++d) g.type[d] = (v[d] == 1 ? 1 : 0) | (v[d] == A.n - 1 ? 2 : 0);
-  // this thread's line of every pass: component lc, coordinates (lu, lv) in the two other directions
-  const int lc = tid / (NPD * NPD), lu = (tid / NPD) % NPD, lv = tid % NPD;
 
   // ---- gather F (velocity boxes in Ba) and G (pressure box in Pp)
   for (int j = tid; j < C::NV + C::NP; j += C::NT) {
@@ -349,13 +381,13 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   __syncthreads();
 
   // ---- Ft = S^T F; Bb = Lam^{-1} Ft / nu
-  patch_pass<K, T, VEL_FWD, 0, 0>(Ba, Bb, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, VEL_FWD, 1, 0>(Bb, Ba, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, VEL_FWD, 2, 0>(Ba, Ft, false, EPI_FT_AND_SCALE, nullptr, Bb, tb, g, lc, lu, lv);
+  patch_pass<K, T, VEL_FWD>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_FWD>(Bb, Ba, 1, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_FWD>(Ba, Ft, 2, 0, false, EPI_FT_AND_SCALE, nullptr, Bb, tb, g);
   // ---- R = sum_c (B_c S_c) Bb_c - G
-  patch_pass<K, T, BF, 0, 0>(Bb, Ba, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, BF, 1, 1>(Ba, Bb, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, BF, 2, 3>(Bb, Ba, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
+  patch_pass<K, T, BF>(Bb, Ba, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BF>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BF>(Bb, Ba, 2, 3, false, EPI_NONE, nullptr, nullptr, tb, g);
   T s1 = T(0), s2 = T(0);
   for (int q = tid; q < C::NP; q += C::NT) {
     const int o = (q % NPD) + BX * (q / NPD);
@@ -380,12 +412,12 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   for (int it = 0; it < A.cg_iters; ++it) {
     if (A.cg_tol_mode && rr <= A.cg_tol * A.cg_tol * rr0) break;
     if (!(rr > T(0))) break;
-    patch_pass<K, T, BT, 0, 0>(Dd, Ba, true, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-    patch_pass<K, T, BT, 1, 1>(Ba, Bb, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-    patch_pass<K, T, BT, 2, 3>(Bb, Ba, false, EPI_SCALE, nullptr, nullptr, tb, g, lc, lu, lv);
-    patch_pass<K, T, BF, 0, 0>(Ba, Bb, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-    patch_pass<K, T, BF, 1, 1>(Bb, Ba, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-    patch_pass<K, T, BF, 2, 3>(Ba, Bb, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
+    patch_pass<K, T, BT>(Dd, Ba, 0, 0, true, EPI_NONE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BT>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BT>(Bb, Ba, 2, 3, false, EPI_SCALE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BF>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BF>(Bb, Ba, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BF>(Ba, Bb, 2, 3, false, EPI_NONE, nullptr, nullptr, tb, g);
     T part = T(0);
     for (int q = tid; q < C::NP; q += C::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
@@ -422,12 +454,12 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   }
 
   // ---- U_c = S_c Lam_c^{-1} (Ft_c - (B_c S_c)^T P) / nu
-  patch_pass<K, T, BT, 0, 0>(Pp, Ba, true, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, BT, 1, 1>(Ba, Bb, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, BT, 2, 3>(Bb, Ba, false, EPI_SUB_SCALE, Ft, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, VEL_BWD, 0, 0>(Ba, Bb, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, VEL_BWD, 1, 0>(Bb, Ba, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
-  patch_pass<K, T, VEL_BWD, 2, 0>(Ba, Bb, false, EPI_NONE, nullptr, nullptr, tb, g, lc, lu, lv);
+  patch_pass<K, T, BT>(Pp, Ba, 0, 0, true, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BT>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BT>(Bb, Ba, 2, 3, false, EPI_SUB_SCALE, Ft, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD>(Bb, Ba, 1, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD>(Ba, Bb, 2, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
 
   // ---- scatter
   for (int j = tid; j < C::NV + C::NP; j += C::NT) {
