@@ -256,6 +256,41 @@ def run_batch(args):
             "iterations": [i["iterations"] for i in infos]}
 
 
+def run_smooth_mode(args):
+    """Time one smoothing step of Algorithm 2 (8 colour residuals + patch solves)
+    on an n^3 mesh in FP32 and FP64; prints one JSON line (ns/DoF per step, the
+    unit of the paper's Table 2 smoothing row)."""
+    import torch
+
+    from paper_2410_09497_gb300 import StokesMG
+    from seeded_inputs import random_vector
+
+    n, k = args.n, args.k
+    out = {"mode": "smooth", "workload": f"one smoothing step, RT_{k} x DGQ_{k}, {n}^3 cells, Schur-CG 15 steps",
+           "unit": "ns/DoF per smoothing step"}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        P = StokesMG(n, k, 1.0, stream=stream)
+        N = P.layout()["n_total"]
+        for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+            b = torch.from_numpy(random_vector(5, N)).to(dt).cuda()
+            x = torch.zeros_like(b)
+            for _ in range(args.warmup):
+                P.smooth(x, b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                P.smooth(x, b)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            out[name] = {"ms_per_step": ms, "ns_per_dof": ms * 1e6 / N, "dofs": N}
+        P.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -420,11 +455,15 @@ def main():
     ap.add_argument("--solve-n", type=int, default=64, help="mesh of the mixed-vs-FP64 solve sub-benchmark (0: skip)")
     ap.add_argument("--solve-k", type=int, default=3)
     ap.add_argument("--batch", type=int, default=0, help="also run N batched uneven solves (0: skip)")
+    ap.add_argument("--mode", default="apply", choices=["apply", "smooth"],
+                    help="apply: the benchmark line; smooth: time smoothing steps only (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "smooth":
+        return run_smooth_mode(args)
     return run_ours(args)
 
 

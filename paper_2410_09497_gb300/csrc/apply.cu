@@ -166,7 +166,7 @@ __device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, cons
 }
 
 template <int K, typename T>
-__global__ void __launch_bounds__(ApplyCfg<K>::NT, (sizeof(T) == 4 && K <= 3 ? 2 : 1)) apply_velocity_kernel(ApplyArgs<T> A) {
+__global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 3 ? 2 : 1)) apply_velocity_kernel(ApplyArgs<T> A) {
   using Cfg = ApplyCfg<K>;
   constexpr int ND = Cfg::ND, NC = Cfg::NC, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
   __shared__ CellTables<T> tab;

@@ -191,3 +191,32 @@ def test_vcycle_and_solve_on_3cube_hierarchy(stk, n, k):
     _, info_ref = H.solve(b, tol=1e-8)
     assert info["converged"] and abs(info["iterations"] - info_ref["iterations"]) <= 1
     P.close()
+
+
+def test_non_convergence_and_bad_arguments_report_status(stk):
+    """Failure paths on the host side of the ABI: an iteration limit that is
+    too small returns STK_ENOCONV with the info filled and the last iterate in
+    x; malformed calls return STK_EINVAL with a message and leave the problem
+    usable."""
+    import torch
+
+    man = Manufactured(manufactured_coefficients(0))
+    d = Discretization(4, 2)
+    b = rhs(d, man)
+    P = stk.StokesMG(4, 2, max_iter=1)
+    x = dev(np.zeros(d.N))
+    info = P.solve(dev(b), x, rtol=1e-12, check=False)
+    assert info["status"] == -4 and not info["converged"] and info["iterations"] == 1
+    assert 0 < info["relres"] < 1 and np.isfinite(x.cpu().numpy()).all()
+    with pytest.raises(stk.StokesError) as err:
+        P.solve(dev(b), x, rtol=1e-12)
+    assert err.value.code == -4
+    # wrong level / dtype / length are rejected before any launch
+    with pytest.raises((stk.StokesError, ValueError)):
+        P.apply(dev(b), x, level=7)
+    with pytest.raises(ValueError):
+        P.apply(dev(b[:-1].copy()), x)
+    y = torch.empty_like(x)
+    P.apply(dev(b), y)  # still usable
+    assert np.isfinite(y.cpu().numpy()).all()
+    P.close()
