@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -129,6 +130,8 @@ struct KrylovWork {
   double* h_host = nullptr;  // pinned
 };
 
+struct Coarse3Factors;  // coarse3.cu
+
 }  // namespace stk
 
 struct stk_problem {
@@ -142,6 +145,7 @@ struct stk_problem {
   double* pmean_w = nullptr;       // device Gauss weights x h of the finest level (pressure mean)
   double* coarse_inv = nullptr;    // dense pseudo-inverse of the 2^3 coarse problem, patch order
   double* coarse3[3] = {nullptr, nullptr, nullptr};  // FP64 b, x, r of a 3^3 coarse mesh
+  std::shared_ptr<stk::Coarse3Factors> coarse3f;      // dense factors of the 3^3 coarse problem (shared)
   stk::MgWork mg[2];               // [STK_F64], [STK_F32]
   stk::KrylovWork kry;
   std::string err;
@@ -163,6 +167,12 @@ cudaError_t launch_patch_colour_cg(const stk_problem* P, int level, int dtype, i
                                    int cg_tol_mode, int cg_iters, double cg_tol);
 cudaError_t launch_coarse_columns(const stk_problem* P, double* cols, int max_iter, double tol);
 cudaError_t launch_coarse_solve(const stk_problem* P, int dtype, const void* b, void* x);
+// coarse3.cu: exact solve on a 3^3 coarse mesh.  acquire_coarse3 builds (or
+// takes from the cache) the dense factors, using P->coarse3 as probes and
+// synchronizing the stream; coarse3_solve maps P->coarse3[0] (pressure rows
+// summing to zero) to P->coarse3[1], with P->coarse3[2] as scratch.
+cudaError_t acquire_coarse3(stk_problem* P);
+cudaError_t coarse3_solve(stk_problem* P);
 // solver.cu
 cudaError_t ensure_mg_workspace(stk_problem* P, int dtype);
 cudaError_t ensure_coarse(stk_problem* P);

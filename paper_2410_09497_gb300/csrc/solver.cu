@@ -3,7 +3,7 @@
 //
 //  smooth  (Algorithm 2): for each colour, r = b - A x, then the patch kernel.
 //  vcycle  (Sec. 3): pre-smooth, residual, restriction, recursion, exact
-//          coarse solve on the 2^3 mesh, prolongation-add, post-smooth; x0 = 0.
+//          coarse solve on the 2^3 or 3^3 mesh, prolongation-add, post-smooth; x0 = 0.
 //  solve   (Sec. 3.3, Sec. 4.3): flexible GMRES(restart), right preconditioned
 //          by one V-cycle, x0 = 0, stopping at ||b - A x|| <= rtol ||b||.  In
 //          mixed precision the V-cycle runs in FP32 and everything else in
@@ -166,14 +166,15 @@ cudaError_t ensure_mg_workspace(stk_problem* P, int dtype) {
 
 cudaError_t ensure_coarse(stk_problem* P) {
   if (P->levels[0].n != 2) {
-    // 3^3 coarse mesh: FP64 vectors for the coarse sweeps
-    if (P->coarse3[0]) return cudaSuccess;
+    // 3^3 coarse mesh: FP64 vectors and the dense block factors
+    if (P->coarse3f) return cudaSuccess;
     const size_t bytes = sizeof(double) * (size_t)P->levels[0].ntotal;
     for (int i = 0; i < 3; ++i) {
+      if (P->coarse3[i]) continue;
       cudaError_t e = cudaMalloc(&P->coarse3[i], bytes);
       if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return acquire_coarse3(P);
   }
   if (P->coarse_inv) return cudaSuccess;
   const int NL = patch_local_size(P->k);
@@ -199,15 +200,11 @@ cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void
   return cudaSuccess;
 }
 
-// Coarse solve P_0^{-1} (Sec. 3).  On the 2^3 mesh: the dense FP64
-// pseudo-inverse.  On a 3^3 mesh (n = 3 * 2^L) the problem has eight
-// overlapping vertex patches, one per colour; the solve is kCoarseSweeps
-// steps of the multiplicative Schwarz iteration in FP64 (local CG to a
-// relative 1e-7), from x = 0, after removing the mean of the pressure rows:
-// each sweep reduces the residual about 2x, so the coarse solve is accurate
-// to about 1e-7 (not exact).
-constexpr int kCoarseSweeps = 24;
-
+// Coarse solve P_0^{-1} (Sec. 3), exact in FP64 whatever the V-cycle's
+// precision.  On the 2^3 mesh: the dense pseudo-inverse.  On a 3^3 mesh
+// (n = 3 * 2^L): block elimination with dense factors of the velocity blocks
+// and of the pressure Schur complement (coarse3.cu), after the pressure rows
+// of the right-hand side are made to sum to zero.
 template <typename S, typename D>
 __global__ void copy_convert_kernel(const S* __restrict__ src, D* __restrict__ dst, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -233,19 +230,14 @@ __global__ void __launch_bounds__(256) remove_pressure_sum(double* __restrict__ 
 static cudaError_t coarse_level_solve(stk_problem* P, int dtype, const void* b, void* x) {
   if (P->levels[0].n == 2) return launch_coarse_solve(P, dtype, b, x);
   const int64_t n = P->levels[0].ntotal;
-  double *cb = P->coarse3[0], *cx = P->coarse3[1], *cr = P->coarse3[2];
+  double *cb = P->coarse3[0], *cx = P->coarse3[1];
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 1024);
   if (dtype == STK_F64)
     copy_convert_kernel<double, double><<<grid, 256, 0, P->stream>>>((const double*)b, cb, n);
   else
     copy_convert_kernel<float, double><<<grid, 256, 0, P->stream>>>((const float*)b, cb, n);
   remove_pressure_sum<<<1, 256, 0, P->stream>>>(cb + 3 * P->levels[0].nvel, P->levels[0].npress);
-  cudaError_t e = cudaMemsetAsync(cx, 0, sizeof(double) * n, P->stream);
-  for (int s = 0; e == cudaSuccess && s < kCoarseSweeps; ++s)
-    for (int colour = 0; e == cudaSuccess && colour < 8; ++colour) {
-      e = launch_apply(P, 0, STK_F64, cx, cb, cr, -1.0);
-      if (e == cudaSuccess) e = launch_patch_colour_cg(P, 0, STK_F64, colour, cr, cx, 1, 60, 1e-7);
-    }
+  cudaError_t e = coarse3_solve(P);
   if (e != cudaSuccess) return e;
   if (dtype == STK_F64)
     copy_convert_kernel<double, double><<<grid, 256, 0, P->stream>>>(cx, (double*)x, n);

@@ -160,19 +160,47 @@ def test_rhs_matches_oracle(stk, n, k, nu):
 
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_coarse_solve_on_3cube(stk, k):
-    """n = 3 * 2^L hierarchies end on a 3^3 mesh, solved by converged Schwarz sweeps."""
+    """n = 3 * 2^L hierarchies end on a 3^3 mesh, solved exactly by block
+    elimination (dense velocity-block inverses and Schur complement)."""
     H = Hierarchy(3, k)
     d = H.levels[0].disc
     b = random_vector(1300 + k, d.N) * d.free_mask()
-    # a consistent right-hand side (what a V-cycle restricts): mean-free pressure rows
-    b[d.offsets[3]:] -= b[d.offsets[3]:].mean()
-    ref = H.coarse_solve(b)
+    ref = H.coarse_solve(b)  # bordered dense LU: the pressure-row mean goes to the multiplier
     P = stk.StokesMG(3, k)
     x = dev(np.full(d.N, np.nan))
     P.coarse_solve(dev(b), x)
-    # 24 converging sweeps: the 3^3 coarse solve is accurate to ~1e-7, not exact
-    assert relerr(x.cpu().numpy(), ref) <= 1e-5
+    assert relerr(x.cpu().numpy(), ref) <= 1e-10
+    # consistent right-hand side, FP32 in and out (the solve itself runs in FP64)
+    b[d.offsets[3]:] -= b[d.offsets[3]:].mean()
+    ref = H.coarse_solve(b)
+    x32 = dev(np.full(d.N, np.nan, dtype=np.float32))
+    P.coarse_solve(dev(b.astype(np.float32)), x32)
+    assert relerr(x32.cpu().numpy().astype(np.float64), ref) <= 1e-5
     P.close()
+
+
+def test_coarse_factors_shared_and_keyed(stk):
+    """The 3^3 factors are shared by problems with the same (k, nu, penalty)
+    and rebuilt for another nu; each problem still solves its own system."""
+    k = 2
+    results = {}
+    for nu, pf in ((1.0, 1.0), (0.37, 1.0), (1.0, 2.5)):
+        H = Hierarchy(3, k, nu=nu, penalty_factor=pf)
+        d = H.levels[0].disc
+        b = random_vector(1350, d.N) * d.free_mask()
+        ref = H.coarse_solve(b)
+        Ps = [stk.StokesMG(3, k, nu, penalty_factor=pf), stk.StokesMG(6, k, nu, penalty_factor=pf)]
+        xs = []
+        for P in Ps:
+            x = dev(np.full(d.N, np.nan))
+            P.coarse_solve(dev(b), x)
+            xs.append(x.cpu().numpy())
+        assert np.array_equal(xs[0], xs[1])  # same factors, same kernels
+        assert relerr(xs[0], ref) <= 1e-10
+        results[(nu, pf)] = xs[0]
+        for P in Ps:
+            P.close()
+    assert not np.allclose(results[(1.0, 1.0)], results[(0.37, 1.0)])
 
 
 @pytest.mark.parametrize("n,k", [(6, 2), (12, 1)])
@@ -185,7 +213,7 @@ def test_vcycle_and_solve_on_3cube_hierarchy(stk, n, k):
     P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
     x = dev(np.full(d.N, np.nan))
     P.vcycle(dev(b), x)
-    assert relerr(x.cpu().numpy(), ref) <= 1e-5
+    assert relerr(x.cpu().numpy(), ref) <= 1e-10
     xs = dev(np.zeros(d.N))
     info = P.solve(dev(b), xs, rtol=1e-8)
     _, info_ref = H.solve(b, tol=1e-8)
