@@ -61,24 +61,36 @@ constexpr int kMaxPD = 2 * kMaxDegree + 2;  // patch nodes, discontinuous direct
 //   FM[t][q][j] = W[q] SD[t][q][j]: the mass factor in the eigenbasis
 // The four transform matrices are stored with rows of kRowStride entries
 // (zero padded, 16-byte aligned) so that kernels read a row with vector loads.
+// Kernels treat every transform as (2k+2) x (2k+2): SC and EC carry a zero row
+// / column 2k+1 and LC[2k+1] = 1, so a padded node of a velocity component's
+// continuous direction stays exactly zero through every pass.
 constexpr int kRowStride = 12;
 template <typename T>
 struct PatchTables {
-  alignas(16) T SC[kMaxPC * kRowStride];
+  alignas(16) T SC[kMaxPD * kRowStride];
   alignas(16) T SD[4][kMaxPD * kRowStride];
   alignas(16) T EC[kMaxPD * kRowStride];
   alignas(16) T FM[4][kMaxPD * kRowStride];
-  T LC[kMaxPC];
+  T LC[kMaxPD];
   T LD[4][kMaxPD];
   T DL[kMaxPD * kMaxPC];
   T W[kMaxPD];
   T inv_nu;
+  // 1 when the eigenvectors of SC / SD[t] are ordered even (symmetric under
+  // the patch reflection) first, odd after: the kernels then transform lines
+  // in the even-odd form (half the products).  Holds for SC and for the
+  // reflection-symmetric types 0 and 3.
+  int eo_c;
+  int eo_d[4];
 };
 
 struct PatchTables1D {
   int k = 0;
   double nu = 1.0;
   std::vector<double> SC, LC, SD[4], LD[4], DL, W;
+  // even-odd ordering (see sort_by_parity): eigenvectors symmetric under the
+  // reflection of the patch come first, antisymmetric ones after
+  bool eo_c = false, eo_d[4] = {false, false, false, false};
 };
 
 void generalized_eigen(int n, const std::vector<double>& K, const std::vector<double>& M, std::vector<double>& S,

@@ -109,6 +109,40 @@ void generalized_eigen(int n, const std::vector<double>& K, const std::vector<do
     }
 }
 
+// Reorders the generalized eigenpairs (columns of S, row-major n x n) of a
+// reflection-symmetric 1D operator so that eigenvectors with v(n-1-i) = v(i)
+// come first and those with v(n-1-i) = -v(i) after.  Returns false (and
+// leaves S, lam unchanged) unless every column has a parity to rounding
+// accuracy and the counts are ceil(n/2) even, floor(n/2) odd.
+static bool sort_by_parity(int n, std::vector<double>& S, std::vector<double>& lam) {
+  std::vector<int> even, odd;
+  for (int j = 0; j < n; ++j) {
+    double ps = 0.0, pa = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double a = S[i * n + j], b = S[(n - 1 - i) * n + j];
+      ps += (a + b) * (a + b);
+      pa += (a - b) * (a - b);
+    }
+    if (pa <= 1e-20 * ps)
+      even.push_back(j);
+    else if (ps <= 1e-20 * pa)
+      odd.push_back(j);
+    else
+      return false;
+  }
+  if ((int)even.size() != (n + 1) / 2) return false;
+  std::vector<int> order(even);
+  order.insert(order.end(), odd.begin(), odd.end());
+  std::vector<double> S2(n * n), l2(n);
+  for (int jn = 0; jn < n; ++jn) {
+    for (int i = 0; i < n; ++i) S2[i * n + jn] = S[i * n + order[jn]];
+    l2[jn] = lam[order[jn]];
+  }
+  S.swap(S2);
+  lam.swap(l2);
+  return true;
+}
+
 PatchTables1D build_patch_tables(const Tables1D& t) {
   const int k = t.k, nc = k + 2, nd = k + 1;
   const int npc = 2 * k + 1, npd = 2 * k + 2;
@@ -131,6 +165,7 @@ PatchTables1D build_patch_tables(const Tables1D& t) {
       Mc[i * npc + j] = M2[(i + 1) * (2 * k + 3) + (j + 1)];
     }
   generalized_eigen(npc, Kc, Mc, P.SC, P.LC);
+  P.eo_c = sort_by_parity(npc, P.SC, P.LC);
   // discontinuous directions, four boundary types
   for (int type = 0; type < 4; ++type) {
     const int t0 = (type & 1) ? 1 : 0;  // lower cell is the first cell of the mesh
@@ -145,6 +180,8 @@ PatchTables1D build_patch_tables(const Tables1D& t) {
       }
     for (int j = 0; j < npd; ++j) Md[j * npd + j] = t.S[j % nd];
     generalized_eigen(npd, Kd, Md, P.SD[type], P.LD[type]);
+    // types 0 and 3 are symmetric under the reflection of the patch
+    P.eo_d[type] = (type == 0 || type == 3) && sort_by_parity(npd, P.SD[type], P.LD[type]);
   }
   // local divergence factor: pressure nodes of the two cells x patch-interior velocity nodes
   P.DL.assign(npd * npc, 0.0);
@@ -169,6 +206,7 @@ void fill_patch_tables(const PatchTables1D& p, PatchTables<T>* out) {
   for (int i = 0; i < npc; ++i)
     for (int j = 0; j < npc; ++j) out->SC[i * RS + j] = (T)p.SC[i * npc + j];
   for (int i = 0; i < npc; ++i) out->LC[i] = (T)p.LC[i];
+  out->LC[npc] = T(1);  // padded node (its coefficients are zero)
   for (int t = 0; t < 4; ++t) {
     for (int i = 0; i < npd; ++i)
       for (int j = 0; j < npd; ++j) out->SD[t][i * RS + j] = (T)p.SD[t][i * npd + j];
@@ -187,6 +225,8 @@ void fill_patch_tables(const PatchTables1D& p, PatchTables<T>* out) {
     for (int q = 0; q < npd; ++q)
       for (int j = 0; j < npd; ++j) out->FM[t][q * RS + j] = (T)(p.W[q] * p.SD[t][q * npd + j]);
   out->inv_nu = (T)(1.0 / p.nu);
+  out->eo_c = p.eo_c ? 1 : 0;
+  for (int t = 0; t < 4; ++t) out->eo_d[t] = p.eo_d[t] ? 1 : 0;
 }
 
 template void fill_patch_tables<double>(const PatchTables1D&, PatchTables<double>*);

@@ -19,7 +19,10 @@
 // and the Schur operator is  S = (1/nu) sum_c (B_c S_c) Lam_c^{-1} (B_c S_c)^T.
 // One CG step is therefore six passes of batched 1D line transforms (three
 // from pressure space to the scaled eigen-coefficients, three back) over all
-// three components, instead of B^T, A^{-1} (six passes) and B separately.
+// three components, instead of B^T, A^{-1} (six passes) and B separately;
+// for k <= 3 the two middle ones run as one pass in registers.  Symmetric
+// 1D eigenbases (the continuous direction, interior patches) transform lines
+// in even-odd form: half the products and matrix loads.
 //   start:  Ft_c = S_c^T F_c,  R = sum_c (B_c S_c) Lam_c^{-1} Ft_c / nu - G
 //   end:    U_c = S_c Lam_c^{-1} (Ft_c - (B_c S_c)^T P) / nu
 // Every patch tensor lives in shared memory in a (2k+3) x (2k+2) x (2k+2)
@@ -42,7 +45,16 @@ struct PatchCfg {
   static constexpr int NP = NPD * NPD * NPD;
   static constexpr int BX = NPD + 1;           // padded x extent of every patch tensor
   static constexpr int BOX = BX * NPD * NPD;   // one padded tensor
-  static constexpr int NT = ((3 * NPD * NPD + 31) / 32) * 32;  // one thread per line of a pass
+  // A pass transforms LPC lines of each component.  W warps serve one
+  // component (warp-uniform component: no divergence) and each thread
+  // transforms R lines with every matrix entry it loads: the broadcast loads
+  // of the transform matrices are what the shared-memory pipe spends most of
+  // its wavefronts on.
+  static constexpr int LPC = NPD * NPD;
+  static constexpr int W = (K <= 3) ? 1 : (K == 4 ? 2 : 3);
+  static constexpr int TPC = 32 * W;
+  static constexpr int R = (LPC + TPC - 1) / TPC;
+  static constexpr int NT = 3 * TPC;
   static constexpr int NW = NT / 32;
 };
 
@@ -50,7 +62,7 @@ struct PatchCfg {
 // memory of one patch (13 padded tensors + tables) permits.
 template <int K, typename T>
 struct PatchOcc {
-  static constexpr int value = sizeof(T) == 4 ? ((K == 1) ? 16 : (K == 2) ? 8 : (K == 3) ? 5 : (K == 4) ? 3 : 2)
+  static constexpr int value = sizeof(T) == 4 ? ((K == 1) ? 12 : (K == 2) ? 8 : (K == 3) ? 6 : (K == 4) ? 3 : 2)
                                               : ((K == 1) ? 8 : (K == 2) ? 4 : (K == 3) ? 3 : 1);
 };
 
@@ -132,14 +144,119 @@ __device__ __forceinline__ void vec_fma(double* r, const double2& w, double s) {
   r[0] += w.x * s;
   r[1] += w.y * s;
 }
-__device__ __forceinline__ float vec_dot(const float4& w, const float* v) {
-  return w.x * v[0] + w.y * v[1] + w.z * v[2] + w.w * v[3];
+__device__ __forceinline__ float vget(const float4& w, int e) { return e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w; }
+__device__ __forceinline__ double vget(const double2& w, int e) { return e == 0 ? w.x : w.y; }
+
+// Even-odd line transforms (Kronbichler-style symmetry of a 1D eigenbasis).
+// The rows of M are indexed by nodes paired by the patch reflection
+// i <-> NR-1-i (P pairs, plus a centre node P when CEN, NR = 2P+1); the
+// columns are eigenvectors, HE even ones then HO odd ones, and
+// M[NR-1-i][j] = SIG s_j M[i][j] with s_j = +1 (even) / -1 (odd).
+// Forward: out_j = sum_i M[i][j] v_i over rows; backward: out_i = sum_j
+// M[i][j] v_j.  Each needs only the first P (+1) rows and half the products.
+// Outputs past the real extent are zero.
+template <int N, int NR, int P, bool CEN, int SIG, int HE, int HO, int R, typename T>
+__device__ __forceinline__ void eo_fwd(const T* __restrict__ M, const T (&v)[R][N], T (&res)[R][N]) {
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::width;
+  constexpr int NCOL = HE + HO, NVEC = (NCOL + VW - 1) / VW;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < N; ++j) res[r][j] = T(0);
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    T a[R], b[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const T x = v[r][i], y = v[r][NR - 1 - i];
+      a[r] = SIG > 0 ? x + y : x - y;  // feeds the even columns
+      b[r] = SIG > 0 ? x - y : x + y;  // feeds the odd columns
+    }
+    const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
+#pragma unroll
+    for (int q = 0; q < NVEC; ++q) {
+      const V w = row[q];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const int j = q * VW + e;
+        if (j < NCOL)
+#pragma unroll
+          for (int r = 0; r < R; ++r) res[r][j] = fma(vget(w, e), j < HE ? a[r] : b[r], res[r][j]);
+      }
+    }
+  }
+  if (CEN) {
+    const V* row = reinterpret_cast<const V*>(M + P * kRowStride);
+#pragma unroll
+    for (int q = 0; q < (HE + VW - 1) / VW; ++q) {
+      const V w = row[q];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const int j = q * VW + e;
+        if (j < HE)
+#pragma unroll
+          for (int r = 0; r < R; ++r) res[r][j] = fma(vget(w, e), v[r][P], res[r][j]);
+      }
+    }
+  }
 }
-__device__ __forceinline__ double vec_dot(const double2& w, const double* v) { return w.x * v[0] + w.y * v[1]; }
+
+template <int N, int NR, int P, bool CEN, int SIG, int HE, int HO, int R, typename T>
+__device__ __forceinline__ void eo_bwd(const T* __restrict__ M, const T (&v)[R][N], T (&res)[R][N]) {
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::width;
+  constexpr int NCOL = HE + HO, NVEC = (NCOL + VW - 1) / VW;
+#pragma unroll
+  for (int i = 0; i < P + (CEN ? 1 : 0); ++i) {
+    const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
+    T E[R], O[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) E[r] = O[r] = T(0);
+#pragma unroll
+    for (int q = 0; q < NVEC; ++q) {
+      const V w = row[q];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const int j = q * VW + e;
+        if (j < HE) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) E[r] = fma(vget(w, e), v[r][j], E[r]);
+        } else if (j < NCOL && i < P) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) O[r] = fma(vget(w, e), v[r][j], O[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (i < P) {
+        res[r][i] = E[r] + O[r];
+        res[r][NR - 1 - i] = SIG > 0 ? E[r] - O[r] : O[r] - E[r];
+      } else {
+        res[r][i] = E[r];  // centre node: odd eigenvectors vanish there
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = NR; j < N; ++j) res[r][j] = T(0);
+}
+
+__device__ __forceinline__ float vec_dot_acc(const float4& w, const float* v, float acc) {
+  acc = fmaf(w.x, v[0], acc);
+  acc = fmaf(w.y, v[1], acc);
+  acc = fmaf(w.z, v[2], acc);
+  return fmaf(w.w, v[3], acc);
+}
+__device__ __forceinline__ double vec_dot_acc(const double2& w, const double* v, double acc) {
+  return fma(w.y, v[1], fma(w.x, v[0], acc));
+}
 
 // pass kinds: velocity eigen-transform (S^T: VEL_FWD, S: VEL_BWD), pressure to
 // eigen-coefficients ((B S)^T: BT), eigen-coefficients to pressure (B S: BF)
-enum { VEL_FWD = 0, VEL_BWD = 1, BT = 2, BF = 3 };
+enum { VEL_FWD = 0, VEL_BWD = 1, BT = 2, BF = 3, BTBF = 4 };
 // epilogues of a pass
 enum { EPI_NONE = 0, EPI_SCALE = 1, EPI_FT_AND_SCALE = 2, EPI_SUB_SCALE = 3 };
 
@@ -148,131 +265,179 @@ struct PatchGeo {
   __device__ __forceinline__ int t(int d) const { return d == 0 ? type[0] : (d == 1 ? type[1] : type[2]); }
 };
 
-// Extent of component c along direction e during a pass of kind MODE, given
-// the directions already transformed in the current chain (bit mask).
-template <int K, int MODE>
-__device__ __forceinline__ int ext_of(int c, int e, int done) {
+// One pass: every line along direction d of the three component tensors.
+// Every tensor is handled as (2k+2)^3 in its padded box: the continuous
+// direction of a velocity component has 2k+1 nodes, the extra node holds zero
+// (zero rows / columns of SC and EC), so all lines have the same length and
+// compile-time loop bounds.  Thread u of component c (warps c W .. c W + W-1)
+// owns lines u, u + TPC, ... of that component.  in_shared: all components
+// read the same (pressure) box.  Epilogues scale by
+// inv_nu / (lam_0 + lam_1 + lam_2) of the output node (the last pass of a
+// chain toward eigen-coefficients).
+// inv_nu / lam: FP32 epilogues use the hardware reciprocal (2 ulp), FP64 the
+// correctly rounded division.
+__device__ __forceinline__ float scale_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double scale_div(double a, double b) { return a / b; }
+
+// R lines through one 1D transform: FWD out_j = sum_i M[i][j] v_i (S^T, (B S)^T),
+// otherwise out_i = sum_j M[i][j] v_j (S, B S).  VELM: velocity eigenvectors
+// (SC / SD[t]) or the divergence / mass factors in the eigenbasis (EC / FM[t]).
+template <int K, typename T, bool FWD, bool VELM, int R>
+__device__ __forceinline__ void line_transform(const T* __restrict__ M, bool eo, bool along_c,
+                                               const T (&v)[R][PatchCfg<K>::NPD], T (&res)[R][PatchCfg<K>::NPD]) {
   using C = PatchCfg<K>;
-  const int vel = (e == c) ? C::NPC : C::NPD;
-  if (MODE == VEL_FWD || MODE == VEL_BWD) return vel;
-  const bool tr = (done >> e) & 1;
-  if (MODE == BT) return tr ? vel : C::NPD;
-  return tr ? C::NPD : vel;  // BF
+  constexpr int N = C::NPD, NPC = C::NPC;
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::width;
+  constexpr int NV = N / VW, TAIL = N - NV * VW;  // N is even: TAIL is 0 or (FP32) 2
+  if (eo) {
+    if (along_c) {
+      if (VELM) {
+        if (FWD)
+          eo_fwd<N, NPC, K, true, 1, K + 1, K, R>(M, v, res);
+        else
+          eo_bwd<N, NPC, K, true, 1, K + 1, K, R>(M, v, res);
+      } else {
+        if (FWD)
+          eo_fwd<N, N, K + 1, false, -1, K + 1, K, R>(M, v, res);
+        else
+          eo_bwd<N, N, K + 1, false, -1, K + 1, K, R>(M, v, res);
+      }
+    } else {
+      if (FWD)
+        eo_fwd<N, N, K + 1, false, 1, K + 1, K + 1, R>(M, v, res);
+      else
+        eo_bwd<N, N, K + 1, false, 1, K + 1, K + 1, R>(M, v, res);
+    }
+  } else if (FWD) {
+    // one vector load feeds VW outputs of R lines
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int j = 0; j < N; ++j) res[r][j] = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const T* row = M + i * kRowStride;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const V w = reinterpret_cast<const V*>(row)[q];
+#pragma unroll
+        for (int r = 0; r < R; ++r) vec_fma(res[r] + q * VW, w, v[r][i]);
+      }
+      if (TAIL) {
+        const float2 w = *reinterpret_cast<const float2*>(row + NV * VW);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          res[r][NV * VW] = fma((T)w.x, v[r][i], res[r][NV * VW]);
+          res[r][NV * VW + 1] = fma((T)w.y, v[r][i], res[r][NV * VW + 1]);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const T* row = M + i * kRowStride;
+      T acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = T(0);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const V w = reinterpret_cast<const V*>(row)[q];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = vec_dot_acc(w, v[r] + q * VW, acc[r]);
+      }
+      if (TAIL) {
+        const float2 w = *reinterpret_cast<const float2*>(row + NV * VW);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          acc[r] = fma((T)w.x, v[r][NV * VW], acc[r]);
+          acc[r] = fma((T)w.y, v[r][NV * VW + 1], acc[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) res[r][i] = acc[r];
+    }
+  }
 }
 
 // One pass: every line along direction d of the three component tensors.
-// in_shared: all components read the same (pressure) box.  Epilogues scale by
+// Every tensor is handled as (2k+2)^3 in its padded box: the continuous
+// direction of a velocity component has 2k+1 nodes, the extra node holds zero
+// (zero rows / columns of SC and EC), so all lines have the same length and
+// compile-time loop bounds.  Thread u of component c (warps c W .. c W + W-1)
+// owns lines u, u + TPC, ... of that component.  in_shared: all components
+// read the same (pressure) box.  Epilogues scale by
 // inv_nu / (lam_0 + lam_1 + lam_2) of the output node (the last pass of a
-// chain toward eigen-coefficients).
-template <int K, typename T, int MODE>
-__device__ void patch_pass_fma(const T* __restrict__ in, T* __restrict__ out, int d, int done, bool in_shared,
-                               int epi, const T* __restrict__ Ft, T* __restrict__ out2, const PatchTables<T>& tb,
-                               const PatchGeo& g) {
+// chain toward eigen-coefficients).  MODE BTBF is the last pass toward the
+// eigen-coefficients, the scaling and the first pass back, fused in registers.
+template <int K, typename T, int MODE, int EPI>
+__device__ __forceinline__ void patch_pass(const T* __restrict__ in, T* __restrict__ out, int d, bool in_shared,
+                                           const T* __restrict__ Ft, T* __restrict__ out2,
+                                           const PatchTables<T>& tb, const PatchGeo& g) {
   using C = PatchCfg<K>;
-  constexpr int NMAX = C::NPD;
+  constexpr int N = C::NPD, LPC = C::LPC, TPC = C::TPC, R = C::R;
+  constexpr bool VELM = (MODE == VEL_FWD || MODE == VEL_BWD);
+  constexpr bool FWD = (MODE == VEL_FWD || MODE == BT || MODE == BTBF);
+  const int c = threadIdx.x / TPC, u = threadIdx.x - c * TPC;
   const int e1 = (d == 0) ? 1 : 0, e2 = (d == 2) ? 1 : 2;
-  int lines[3];
+  const int sd = box_stride(d, C::BX, N);
+  const bool along_c = (d == c);
+  const int td = g.t(d);
+  const T* M = VELM ? (along_c ? tb.SC : tb.SD[td]) : (along_c ? tb.EC : tb.FM[td]);
+  const bool eo = along_c ? (tb.eo_c != 0) : (tb.eo_d[td] != 0);
+  const T* src = in + (in_shared ? 0 : c * C::BOX);
+  int i1[R], i2[R], base[R];
+  bool ok[R];
+  T v[R][N], res[R][N];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) lines[c] = ext_of<K, MODE>(c, e1, done) * ext_of<K, MODE>(c, e2, done);
-  const int total = lines[0] + lines[1] + lines[2];
-  const int sd = box_stride(d, C::BX, C::NPD);
-  for (int L = threadIdx.x; L < total; L += C::NT) {
-    int c = 0, l = L;
-    if (l >= lines[0]) {
-      l -= lines[0];
-      c = 1;
-      if (l >= lines[1]) {
-        l -= lines[1];
-        c = 2;
-      }
+  for (int r = 0; r < R; ++r) {
+    const int l = u + r * TPC;
+    ok[r] = l < LPC;
+    const int ll = ok[r] ? l : 0;
+    i1[r] = ll % N;
+    i2[r] = ll / N;
+    base[r] = i1[r] * box_stride(e1, C::BX, N) + i2[r] * box_stride(e2, C::BX, N);
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[r][i] = src[base[r] + i * sd];
+  }
+  line_transform<K, T, FWD, VELM, R>(M, eo, along_c, v, res);
+  // eigenvalues of the two fixed directions, then of the pass direction
+  T lam_fixed[R];
+  const T* lam_d = along_c ? tb.LC : tb.LD[td];
+  if (EPI != EPI_NONE || MODE == BTBF) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      lam_fixed[r] = ((e1 == c) ? tb.LC[i1[r]] : tb.LD[g.t(e1)][i1[r]]) +
+                     ((e2 == c) ? tb.LC[i2[r]] : tb.LD[g.t(e2)][i2[r]]);
+  }
+  if (MODE == BTBF) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const T ld = lam_d[j];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r][j] = scale_div(tb.inv_nu, lam_fixed[r] + ld) * res[r][j];
     }
-    // the extent along e1 is NPC or NPD: divide by compile-time constants
-    const int x1 = ext_of<K, MODE>(c, e1, done);
-    int i1, i2;
-    if (x1 == C::NPC) {
-      i1 = l % C::NPC;
-      i2 = l / C::NPC;
+    line_transform<K, T, false, false, R>(M, eo, along_c, v, res);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (!ok[r]) continue;
+    T* dst = out + c * C::BOX + base[r];
+    if (EPI == EPI_NONE) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) dst[j * sd] = res[r][j];
     } else {
-      i1 = l % C::NPD;
-      i2 = l / C::NPD;
-    }
-    const int base = i1 * box_stride(e1, C::BX, C::NPD) + i2 * box_stride(e2, C::BX, C::NPD);
-    const T* src = in + (in_shared ? 0 : c * C::BOX) + base;
-    T* dst = out + c * C::BOX + base;
-    const bool along_c = (d == c);
-    int n_in, n_out;
-    const T* M;  // rows of kRowStride entries, zero padded
-    if (MODE == VEL_FWD || MODE == VEL_BWD) {
-      n_in = n_out = along_c ? C::NPC : C::NPD;
-      M = along_c ? tb.SC : tb.SD[g.t(d)];
-    } else if (MODE == BT) {
-      n_in = C::NPD;
-      n_out = along_c ? C::NPC : C::NPD;
-      M = along_c ? tb.EC : tb.FM[g.t(d)];
-    } else {
-      n_in = along_c ? C::NPC : C::NPD;
-      n_out = C::NPD;
-      M = along_c ? tb.EC : tb.FM[g.t(d)];
-    }
-    using V = typename Vec16<T>::type;
-    constexpr int VW = Vec16<T>::width;
-    constexpr int NP4 = ((NMAX + VW - 1) / VW) * VW;  // padded row length read per row
-    T v[NP4];
 #pragma unroll
-    for (int i = 0; i < NP4; ++i) v[i] = (i < n_in) ? src[i * sd] : T(0);
-    // eigenvalues of the two fixed directions (scaling epilogues only)
-    T lam_fixed = T(0);
-    if (epi != EPI_NONE) {
-      const int ii[2] = {i1, i2};
-      const int ee[2] = {e1, e2};
-#pragma unroll
-      for (int q = 0; q < 2; ++q) lam_fixed += (ee[q] == c) ? tb.LC[ii[q]] : tb.LD[g.t(ee[q])][ii[q]];
-    }
-    T res[NP4];
-    if (MODE == VEL_FWD || MODE == BT) {
-      // out_j = sum_i M[i][j] v_i: one vector load feeds VW outputs
-#pragma unroll
-      for (int j = 0; j < NP4; ++j) res[j] = T(0);
-#pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        if (i >= n_in) break;
-        const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
-#pragma unroll
-        for (int q = 0; q < NP4 / VW; ++q) {
-          const V w = row[q];
-          vec_fma(res + q * VW, w, v[i]);
-        }
-      }
-    } else {
-      // out_i = sum_j M[i][j] v_j
-#pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        res[i] = T(0);
-        if (i >= n_out) continue;
-        const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
-        T acc = T(0);
-#pragma unroll
-        for (int q = 0; q < NP4 / VW; ++q) acc += vec_dot(row[q], v + q * VW);
-        res[i] = acc;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < NMAX; ++j) {
-      if (j >= n_out) break;
-      const T acc = res[j];
-      const int o = j * sd;
-      if (epi == EPI_NONE) {
-        dst[o] = acc;
-      } else {
-        const T lam = lam_fixed + (along_c ? tb.LC[j] : tb.LD[g.t(d)][j]);
-        const T inv = tb.inv_nu / lam;
-        if (epi == EPI_SCALE) {
-          dst[o] = inv * acc;
-        } else if (epi == EPI_FT_AND_SCALE) {
-          dst[o] = acc;                                   // Ft = S^T F
-          out2[c * C::BOX + base + o] = inv * acc;        // Lam^{-1} Ft / nu
+      for (int j = 0; j < N; ++j) {
+        const int o = j * sd;
+        const T inv = scale_div(tb.inv_nu, lam_fixed[r] + lam_d[j]);
+        if (EPI == EPI_SCALE) {
+          dst[o] = inv * res[r][j];
+        } else if (EPI == EPI_FT_AND_SCALE) {
+          dst[o] = res[r][j];                                // Ft = S^T F
+          out2[c * C::BOX + base[r] + o] = inv * res[r][j];  // Lam^{-1} Ft / nu
         } else {
-          dst[o] = inv * (Ft[c * C::BOX + base + o] - acc);
+          dst[o] = inv * (Ft[c * C::BOX + base[r] + o] - res[r][j]);
         }
       }
     }
@@ -280,11 +445,10 @@ __device__ void patch_pass_fma(const T* __restrict__ in, T* __restrict__ out, in
   __syncthreads();
 }
 
-template <int K, typename T, int MODE>
-__device__ __forceinline__ void patch_pass(const T* in, T* out, int d, int done, bool in_shared, int epi, const T* Ft,
-                                           T* out2, const PatchTables<T>& tb, const PatchGeo& g) {
-  patch_pass_fma<K, T, MODE>(in, out, d, done, in_shared, epi, Ft, out2, tb, g);
-}
+// The z pass toward the eigen-coefficients, the scaling and the z pass back
+// run fused in registers where the two line buffers fit (k <= 3).
+template <int K>
+constexpr bool kFuseZ = K <= 3;
 
 // global index of the local velocity node (c; i0, i1, i2) or pressure node (c = 3)
 template <int K>
@@ -345,8 +509,20 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   T* SD = Pp + BOX;                          // S applied to the search direction
 
   const int tid = threadIdx.x;
-  for (int i = tid; i < (int)(sizeof(PatchTables<T>) / sizeof(T)); i += C::NT)
-    reinterpret_cast<T*>(&tb)[i] = reinterpret_cast<const T*>(A.tab)[i];
+  constexpr int NL = C::NV + C::NP;  // patch-local DoFs
+  constexpr int UG = 8;              // global loads a thread has in flight in gather and scatter
+  {
+    // tables: 16-byte copies, all issued before the first store
+    constexpr int NQ = (int)(sizeof(PatchTables<T>) / 16), UQ = (NQ + C::NT - 1) / C::NT;
+    const int4* src = reinterpret_cast<const int4*>(A.tab);
+    int4 q[UQ];
+#pragma unroll
+    for (int u = 0; u < UQ; ++u)
+      if (tid + u * C::NT < NQ) q[u] = src[tid + u * C::NT];
+#pragma unroll
+    for (int u = 0; u < UQ; ++u)
+      if (tid + u * C::NT < NQ) reinterpret_cast<int4*>(&tb)[tid + u * C::NT] = q[u];
+  }
 
   int v[3];
   if (A.mode == 0) {
@@ -363,31 +539,46 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   PatchGeo g;
   for (int d = 0; d < 3; ++d) g.type[d] = (v[d] == 1 ? 1 : 0) | (v[d] == A.n - 1 ? 2 : 0);
 
-  // ---- gather F (velocity boxes in Ba) and G (pressure box in Pp)
-  for (int j = tid; j < C::NV + C::NP; j += C::NT) {
-    int c, i0, i1, i2;
-    patch_local_decode<K>(j, c, i0, i1, i2);
-    T val;
-    if (A.mode == 0)
-      val = A.r[patch_node_global<K>(c, i0, i1, i2, v, A.m)];
-    else
-      val = (j == (int)blockIdx.x) ? T(1) : T(0);
-    const int o = i0 + BX * (i1 + NPD * i2);
-    if (c < 3)
-      Ba[c * BOX + o] = val;
-    else
-      Pp[o] = val;
+  // ---- gather F (velocity boxes in Ba) and G (pressure box in Pp = Ba + 8 BOX);
+  // the padded plane (node 2k+1 of the continuous direction) of each velocity
+  // box is set to zero.  UG loads per thread are issued before their stores.
+  for (int j0 = tid; j0 < NL; j0 += C::NT * UG) {
+    T val[UG];
+    int dst[UG];
+#pragma unroll
+    for (int u = 0; u < UG; ++u) {
+      const int j = j0 + u * C::NT;
+      dst[u] = -1;
+      val[u] = T(0);
+      if (j < NL) {
+        int c, i0, i1, i2;
+        patch_local_decode<K>(j, c, i0, i1, i2);
+        dst[u] = (c < 3 ? c * BOX : 8 * BOX) + i0 + BX * (i1 + NPD * i2);
+        if (A.mode == 0)
+          val[u] = A.r[patch_node_global<K>(c, i0, i1, i2, v, A.m)];
+        else
+          val[u] = (j == (int)blockIdx.x) ? T(1) : T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UG; ++u)
+      if (dst[u] >= 0) Ba[dst[u]] = val[u];
+  }
+  for (int i = tid; i < 3 * NPD * NPD; i += C::NT) {
+    const int c = i / (NPD * NPD), a = i % NPD, b = (i / NPD) % NPD;
+    const int ii[3] = {c == 0 ? C::NPC : a, c == 1 ? C::NPC : (c == 0 ? a : b), c == 2 ? C::NPC : b};
+    Ba[c * BOX + ii[0] + BX * (ii[1] + NPD * ii[2])] = T(0);
   }
   __syncthreads();
 
   // ---- Ft = S^T F; Bb = Lam^{-1} Ft / nu
-  patch_pass<K, T, VEL_FWD>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
-  patch_pass<K, T, VEL_FWD>(Bb, Ba, 1, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
-  patch_pass<K, T, VEL_FWD>(Ba, Ft, 2, 0, false, EPI_FT_AND_SCALE, nullptr, Bb, tb, g);
+  patch_pass<K, T, VEL_FWD, EPI_NONE>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_FWD, EPI_NONE>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_FWD, EPI_FT_AND_SCALE>(Ba, Ft, 2, false, nullptr, Bb, tb, g);
   // ---- R = sum_c (B_c S_c) Bb_c - G
-  patch_pass<K, T, BF>(Bb, Ba, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
-  patch_pass<K, T, BF>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
-  patch_pass<K, T, BF>(Bb, Ba, 2, 3, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BF, EPI_NONE>(Bb, Ba, 0, false, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BF, EPI_NONE>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BF, EPI_NONE>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
   T s1 = T(0), s2 = T(0);
   for (int q = tid; q < C::NP; q += C::NT) {
     const int o = (q % NPD) + BX * (q / NPD);
@@ -412,16 +603,26 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   for (int it = 0; it < A.cg_iters; ++it) {
     if (A.cg_tol_mode && rr <= A.cg_tol * A.cg_tol * rr0) break;
     if (!(rr > T(0))) break;
-    patch_pass<K, T, BT>(Dd, Ba, 0, 0, true, EPI_NONE, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BT>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BT>(Bb, Ba, 2, 3, false, EPI_SCALE, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BF>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BF>(Bb, Ba, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BF>(Ba, Bb, 2, 3, false, EPI_NONE, nullptr, nullptr, tb, g);
+    // SDc = S d per component: (B S) Lam^{-1} (B S)^T d, passes x, y, z then z, y, x
+    patch_pass<K, T, BT, EPI_NONE>(Dd, Ba, 0, true, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BT, EPI_NONE>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
+    T* SDc;
+    if constexpr (kFuseZ<K>) {
+      patch_pass<K, T, BTBF, EPI_NONE>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE>(Bb, Ba, 0, false, nullptr, nullptr, tb, g);
+      SDc = Ba;
+    } else {
+      patch_pass<K, T, BT, EPI_SCALE>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE>(Ba, Bb, 2, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
+      SDc = Bb;
+    }
     T part = T(0);
     for (int q = tid; q < C::NP; q += C::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
-      const T s = Bb[o] + Bb[BOX + o] + Bb[2 * BOX + o];
+      const T s = SDc[o] + SDc[BOX + o] + SDc[2 * BOX + o];
       SD[o] = s;
       part += Dd[o] * s;
     }
@@ -454,23 +655,42 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   }
 
   // ---- U_c = S_c Lam_c^{-1} (Ft_c - (B_c S_c)^T P) / nu
-  patch_pass<K, T, BT>(Pp, Ba, 0, 0, true, EPI_NONE, nullptr, nullptr, tb, g);
-  patch_pass<K, T, BT>(Ba, Bb, 1, 1, false, EPI_NONE, nullptr, nullptr, tb, g);
-  patch_pass<K, T, BT>(Bb, Ba, 2, 3, false, EPI_SUB_SCALE, Ft, nullptr, tb, g);
-  patch_pass<K, T, VEL_BWD>(Ba, Bb, 0, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
-  patch_pass<K, T, VEL_BWD>(Bb, Ba, 1, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
-  patch_pass<K, T, VEL_BWD>(Ba, Bb, 2, 0, false, EPI_NONE, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BT, EPI_NONE>(Pp, Ba, 0, true, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BT, EPI_NONE>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BT, EPI_SUB_SCALE>(Bb, Ba, 2, false, Ft, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD, EPI_NONE>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD, EPI_NONE>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
+  patch_pass<K, T, VEL_BWD, EPI_NONE>(Ba, Bb, 2, false, nullptr, nullptr, tb, g);
 
-  // ---- scatter
-  for (int j = tid; j < C::NV + C::NP; j += C::NT) {
-    int c, i0, i1, i2;
-    patch_local_decode<K>(j, c, i0, i1, i2);
-    const int o = i0 + BX * (i1 + NPD * i2);
-    const T val = (c < 3) ? Bb[c * BOX + o] : Pp[o];
-    if (A.mode == 0)
-      A.x[patch_node_global<K>(c, i0, i1, i2, v, A.m)] += val;
-    else
-      A.cols[(int64_t)blockIdx.x * (C::NV + C::NP) + j] = (double)val;
+  // ---- scatter: x += (U, P); UG loads of x per thread in flight
+  for (int j0 = tid; j0 < NL; j0 += C::NT * UG) {
+    T val[UG], old[UG];
+    int64_t gi[UG];
+#pragma unroll
+    for (int u = 0; u < UG; ++u) {
+      const int j = j0 + u * C::NT;
+      gi[u] = -1;
+      val[u] = T(0);
+      if (j < NL) {
+        int c, i0, i1, i2;
+        patch_local_decode<K>(j, c, i0, i1, i2);
+        const int o = i0 + BX * (i1 + NPD * i2);
+        val[u] = (c < 3) ? Bb[c * BOX + o] : Pp[o];
+        gi[u] = A.mode == 0 ? patch_node_global<K>(c, i0, i1, i2, v, A.m) : (int64_t)blockIdx.x * NL + j;
+      }
+    }
+    if (A.mode == 0) {
+#pragma unroll
+      for (int u = 0; u < UG; ++u)
+        if (gi[u] >= 0) old[u] = A.x[gi[u]];
+#pragma unroll
+      for (int u = 0; u < UG; ++u)
+        if (gi[u] >= 0) A.x[gi[u]] = old[u] + val[u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < UG; ++u)
+        if (gi[u] >= 0) A.cols[gi[u]] = (double)val[u];
+    }
   }
 }
 
