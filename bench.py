@@ -9,6 +9,13 @@ larger than the 129 MB L2, so no flush is needed between steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The same JSON line carries sub-benchmarks of the other workloads: `sweep`
+(FP64 apply, 64^3 cells, k = 1..5), `smooth` (one smoothing step, 64^3,
+k = 3, FP32 and FP64), `solve` (manufactured problem on 96^3 cells, k = 3,
+to 1e-8: mixed precision against plain FP64) and `batch` (64 uneven
+problems solved together against one after another); each can be resized or
+skipped with its flag (0 skips).
+
 N > 1 runs under torchrun, one independent replica per GPU (the path has no
 data exchange between problems: weak scaling); rank 0 prints one JSON line.
 `--impl reference` times the CPU oracle (the assembled CSR matrix of the
@@ -256,6 +263,74 @@ def run_batch(args):
             "iterations": [i["iterations"] for i in infos]}
 
 
+def run_sweep(args, stream):
+    """FP64 apply throughput over the degrees k = 1..5 on an n^3 mesh (the
+    operator sweep); L2 is flushed between timed applies when x and y fit in it."""
+    import torch
+
+    from paper_2410_09497_gb300 import StokesMG, layout_sizes
+    from seeded_inputs import random_vector
+
+    n = args.sweep_n
+    out = {"workload": f"FP64 Stokes apply, {n}^3 cells, k = 1..5", "unit": "GDoF/s", "per_k": {}}
+    flush = torch.empty(64 * 2**20, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    with torch.cuda.stream(stream):
+        for k in range(1, 6):
+            P = StokesMG(n, k, 1.0, stream=stream)
+            nv, npress, N = layout_sizes(n, k)
+            x = torch.from_numpy(random_vector(2000 + k, N)).cuda()
+            y = torch.empty_like(x)
+            needs_flush = 2 * N * 8 < 2 * 129 * 10**6
+            for _ in range(3):
+                P.apply(x, y)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for a, b in ev:
+                if needs_flush:
+                    flush.zero_()
+                a.record(stream)
+                P.apply(x, y)
+                b.record(stream)
+            torch.cuda.synchronize()
+            t = sum(a.elapsed_time(b) for a, b in ev) / len(ev) / 1e3
+            flops = velocity_flops_per_dof(k) * 3 * nv + pressure_flops_per_dof(k) * npress
+            out["per_k"][str(k)] = {"dofs": N, "gdofs": N / t / 1e9, "ms": t * 1e3,
+                                    "frac_fp64_peak": flops / t / 1e12 / FP64_PEAK_TFLOPS,
+                                    "l2": "flushed between applies" if needs_flush else "inputs larger than L2"}
+            P.close()
+            del x, y
+    return out
+
+
+def run_smooth_pair(args, stream):
+    """One smoothing step (Algorithm 2: 8 colour residuals and patch solves) in
+    FP32 and FP64, ns/DoF (the unit of the paper's smoothing-step row)."""
+    import torch
+
+    from paper_2410_09497_gb300 import StokesMG
+    from seeded_inputs import random_vector
+
+    n, k = args.smooth_n, args.solve_k
+    out = {"workload": f"one smoothing step, RT_{k} x DGQ_{k}, {n}^3 cells, Schur-CG 15 steps", "unit": "ns/DoF"}
+    with torch.cuda.stream(stream):
+        P = StokesMG(n, k, 1.0, stream=stream)
+        N = P.layout()["n_total"]
+        for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+            b = torch.from_numpy(random_vector(5, N)).to(dt).cuda()
+            x = torch.zeros_like(b)
+            for _ in range(2):
+                P.smooth(x, b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                P.smooth(x, b)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            out[name] = {"ms_per_step": ms, "ns_per_dof": ms * 1e6 / N, "dofs": N}
+        P.close()
+    return out
+
+
 def run_smooth_mode(args):
     """Time one smoothing step of Algorithm 2 (8 colour residuals + patch solves)
     on an n^3 mesh in FP32 and FP64; prints one JSON line (ns/DoF per step, the
@@ -421,6 +496,10 @@ def run_ours(args):
         "gpu_launches": 2 * K,
         "clocks": clk.summary(),
     }
+    if args.sweep_n > 0:
+        line["sweep"] = run_sweep(args, stream)
+    if args.smooth_n > 0:
+        line["smooth"] = run_smooth_pair(args, stream)
     if args.solve_n > 0:
         line["solve"] = run_solve_pair(args, stream, ws)
     if args.batch > 0:
@@ -452,9 +531,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-reps", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--solve-n", type=int, default=64, help="mesh of the mixed-vs-FP64 solve sub-benchmark (0: skip)")
+    ap.add_argument("--solve-n", type=int, default=96, help="mesh of the mixed-vs-FP64 solve sub-benchmark (0: skip)")
     ap.add_argument("--solve-k", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=0, help="also run N batched uneven solves (0: skip)")
+    ap.add_argument("--sweep-n", type=int, default=64, help="mesh of the FP64 apply sweep over k = 1..5 (0: skip)")
+    ap.add_argument("--smooth-n", type=int, default=64, help="mesh of the smoothing-step sub-benchmark (0: skip)")
+    ap.add_argument("--batch", type=int, default=64, help="batched uneven solves (0: skip)")
     ap.add_argument("--mode", default="apply", choices=["apply", "smooth"],
                     help="apply: the benchmark line; smooth: time smoothing steps only (profiling)")
     args = ap.parse_args()

@@ -39,7 +39,7 @@ struct ApplyArgs {
 template <int K>
 struct ApplyCfg {
   static constexpr int ND = K + 1, NC = K + 2;
-  static constexpr int BJ = (K == 1) ? 8 : (K == 2) ? 5 : (K == 3) ? 4 : 3;  // cells per tile side
+  static constexpr int BJ = (K == 1) ? 8 : (K == 2) ? 5 : (K == 3) ? 4 : (K == 4) ? 3 : 2;  // cells per tile side
   static constexpr int TJ = BJ * ND;                                          // nodes per tile side
   static constexpr int H = ND;                                                // halo width (one cell)
   static constexpr int J = TJ + 2 * H;                                        // staged extent
@@ -165,8 +165,12 @@ __device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, cons
     if (pl.sidx[i] >= 0) U[pl.sidx[i]] = regs[i];
 }
 
+// Resident CTAs per SM: 2 for k <= 4, 3 for the 2-cell tiles of k = 5.  One
+// CTA per SM (the register count the compiler picks unbounded) left the FP64
+// pipe half idle at k = 4 and 5; the register cap costs a few spills there and
+// measured 1.2-1.3x faster at 64^3.
 template <int K, typename T>
-__global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 3 ? 2 : 1)) apply_velocity_kernel(ApplyArgs<T> A) {
+__global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_velocity_kernel(ApplyArgs<T> A) {
   using Cfg = ApplyCfg<K>;
   constexpr int ND = Cfg::ND, NC = Cfg::NC, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
   __shared__ CellTables<T> tab;
