@@ -366,6 +366,31 @@ def run_smooth_mode(args):
     return 0
 
 
+def run_solve_mode(args):
+    """One mixed-precision solve of the manufactured problem after a warm-up
+    solve (profiling); prints one JSON line."""
+    import torch
+
+    from paper_2410_09497_gb300 import PREC_MIXED, StokesMG
+    from seeded_inputs import manufactured_coefficients
+
+    n, k = args.solve_n, args.solve_k
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        P = StokesMG(n, k, 1.0, precision=PREC_MIXED, stream=stream)
+        b = torch.empty(P.layout()["n_total"], dtype=torch.float64, device="cuda")
+        P.rhs(manufactured_coefficients(3000), b)
+        x = torch.zeros_like(b)
+        P.solve(b, x, 1e-8)
+        t0 = time.perf_counter()
+        info = P.solve(b, x, 1e-8)
+        dt = time.perf_counter() - t0
+        P.close()
+    print(json.dumps({"mode": "solve", "workload": f"mixed-precision solve, RT_{k} x DGQ_{k}, {n}^3 cells, to 1e-8",
+                      "seconds": dt, "iterations": info["iterations"], "relres": info["relres"]}), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -536,8 +561,9 @@ def main():
     ap.add_argument("--sweep-n", type=int, default=64, help="mesh of the FP64 apply sweep over k = 1..5 (0: skip)")
     ap.add_argument("--smooth-n", type=int, default=64, help="mesh of the smoothing-step sub-benchmark (0: skip)")
     ap.add_argument("--batch", type=int, default=64, help="batched uneven solves (0: skip)")
-    ap.add_argument("--mode", default="apply", choices=["apply", "smooth"],
-                    help="apply: the benchmark line; smooth: time smoothing steps only (profiling)")
+    ap.add_argument("--mode", default="apply", choices=["apply", "smooth", "solve"],
+                    help="apply: the benchmark line; smooth / solve: time smoothing steps or one "
+                         "mixed-precision solve only (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -545,6 +571,8 @@ def main():
         return run_reference(args)
     if args.mode == "smooth":
         return run_smooth_mode(args)
+    if args.mode == "solve":
+        return run_solve_mode(args)
     return run_ours(args)
 
 

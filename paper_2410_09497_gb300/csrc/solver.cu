@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <thread>
 
 #include "internal.h"
 
@@ -577,23 +578,32 @@ int run_solve_batch(stk_problem* const* Ps, int count, const double* const* b, d
       return M[i].status;
     }
   }
-  // every round issues one phase of each unfinished solve, then completes them
-  int active = count;
+  // Each solve advances on its own: whenever its stream has drained, its
+  // phase is completed on the host and the next one issued at once, so a
+  // short phase of a small problem never waits for a long phase of a large
+  // one.  The loop polls the streams (cudaStreamQuery) until all are done.
+  int active = 0;
+  for (auto& m : M) {
+    m.issue();
+    if (m.phase != SolveMachine::DONE) ++active;
+  }
   while (active > 0) {
-    for (auto& m : M)
-      if (m.phase != SolveMachine::DONE) m.issue();
-    active = 0;
+    bool progressed = false;
     for (int i = 0; i < count; ++i) {
       SolveMachine& m = M[i];
       if (m.phase == SolveMachine::DONE) continue;
-      cudaError_t e = cudaStreamSynchronize(m.s());
-      if (e != cudaSuccess) {
-        m.fail_cuda(e, "solve");
-        continue;
+      const cudaError_t q = cudaStreamQuery(m.s());
+      if (q == cudaErrorNotReady) continue;
+      progressed = true;
+      if (q != cudaSuccess) {
+        m.fail_cuda(q, "solve");
+      } else {
+        m.complete();
+        if (m.phase != SolveMachine::DONE) m.issue();
       }
-      m.complete();
-      if (m.phase != SolveMachine::DONE) ++active;
+      if (m.phase == SolveMachine::DONE) --active;
     }
+    if (!progressed) std::this_thread::yield();
   }
   int worst = STK_OK;
   for (int i = 0; i < count; ++i)
