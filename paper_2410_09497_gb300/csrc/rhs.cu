@@ -5,7 +5,8 @@
 // The stream functions are seeded sums  psi_c = sum_t amp[c][t] G_a(x) G_b(y) G_c(z),
 // G_a(s) = s^2 (1-s)^2 sin(a pi s), and p = sum_t pamp[t] cos(a pi x) cos(b pi y) cos(c pi z)
 // (the paper's own psi uses constants it does not state).  All derivatives
-// are exact: G^(n) follows from the Leibniz rule.  One CTA per cell evaluates
+// are exact: G^(n) follows from the Leibniz rule.  One CTA per cell tabulates
+// the 1D factors at its quadrature points (one sincos per factor), evaluates
 // f at the quadrature points and contracts it with the 1D bases one direction
 // at a time; nodes on a cell face normal to a component's continuous
 // direction receive two atomic contributions onto a zeroed vector.
@@ -39,19 +40,20 @@ __device__ __forceinline__ double poly_d(double s, int n) {
   return 0.0;
 }
 
-// G_a^(n)(s), n <= 3, by the Leibniz rule
-__device__ double G_d(int a, double s, int n) {
+// G_a^(n)(s) for n = 0..3 by the Leibniz rule, from one sincos
+__device__ void G_all(int a, double s, double* out) {
   const double w = a * M_PI;
   double sv, cv;
   sincos(w * s, &sv, &cv);
   const double trig[4] = {sv, cv, -sv, -cv};  // sin(ws + j pi/2)
   const int binom[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
-  double out = 0.0, wp = 1.0;
-  // term j: C(n, j) P^(j) w^(n-j) sin(ws + (n-j) pi/2)
-  double wpow[4] = {1.0, w, w * w, w * w * w};
-  for (int j = 0; j <= n; ++j) out += binom[n][j] * poly_d(s, j) * wpow[n - j] * trig[(n - j) & 3];
-  (void)wp;
-  return out;
+  const double wpow[4] = {1.0, w, w * w, w * w * w};
+  for (int n = 0; n < 4; ++n) {
+    // term j: C(n, j) P^(j) w^(n-j) sin(ws + (n-j) pi/2)
+    double acc = 0.0;
+    for (int j = 0; j <= n; ++j) acc += binom[n][j] * poly_d(s, j) * wpow[n - j] * trig[(n - j) & 3];
+    out[n] = acc;
+  }
 }
 
 template <int K>
@@ -61,13 +63,25 @@ __global__ void __launch_bounds__(256) rhs_kernel(const RhsParams P, double* __r
   __shared__ double F[3][NQ3];
   __shared__ double T1[NQ * NQ * NC];
   __shared__ double T2[NQ * NC * NC];
+  // the 1D factors of the cell, tabulated once: G[c][t][d][q][n] = G^(n) of
+  // term t of psi_c in direction d at quadrature point q; Pt: sin, cos of the
+  // pressure terms
+  __shared__ double G[3][3][3][NQ][4];
+  __shared__ double Pt[3][3][NQ][2];
   const int cell = blockIdx.x;
   const int cidx[3] = {cell % P.n, (cell / P.n) % P.n, cell / (P.n * P.n)};
+  for (int i = threadIdx.x; i < 27 * NQ; i += blockDim.x) {
+    const int q = i % NQ, d = (i / NQ) % 3, t = (i / (3 * NQ)) % 3, c = i / (9 * NQ);
+    G_all(P.psi_freq[c][t][d], (cidx[d] + P.xq[q]) * P.h, G[c][t][d][q]);
+  }
+  for (int i = threadIdx.x; i < 9 * NQ; i += blockDim.x) {
+    const int q = i % NQ, d = (i / NQ) % 3, t = i / (3 * NQ);
+    sincos(P.p_freq[t][d] * M_PI * (cidx[d] + P.xq[q]) * P.h, &Pt[t][d][q][0], &Pt[t][d][q][1]);
+  }
+  __syncthreads();
   // ---- forcing at the quadrature points, times the quadrature weight
   for (int q = threadIdx.x; q < NQ3; q += blockDim.x) {
     const int qi[3] = {q % NQ, (q / NQ) % NQ, q / (NQ * NQ)};
-    double X[3];
-    for (int d = 0; d < 3; ++d) X[d] = (cidx[d] + P.xq[qi[d]]) * P.h;
     const double W = P.wq[qi[0]] * P.wq[qi[1]] * P.wq[qi[2]] * P.h * P.h * P.h;
     // d_e Laplace(psi_c) for all c, e
     double dl[3][3];
@@ -75,9 +89,7 @@ __global__ void __launch_bounds__(256) rhs_kernel(const RhsParams P, double* __r
       for (int e = 0; e < 3; ++e) dl[c][e] = 0.0;
     for (int c = 0; c < 3; ++c)
       for (int t = 0; t < 3; ++t) {
-        double g[3][4];
-        for (int d = 0; d < 3; ++d)
-          for (int o = 0; o < 4; ++o) g[d][o] = G_d(P.psi_freq[c][t][d], X[d], o);
+        const double* g[3] = {G[c][t][0][qi[0]], G[c][t][1][qi[1]], G[c][t][2][qi[2]]};
         const double A = P.psi_amp[c][t];
         for (int e = 0; e < 3; ++e) {
           double s = 0.0;
@@ -95,7 +107,10 @@ __global__ void __launch_bounds__(256) rhs_kernel(const RhsParams P, double* __r
     double gp[3] = {0.0, 0.0, 0.0};
     for (int t = 0; t < 3; ++t) {
       double cs[3], sn[3];
-      for (int d = 0; d < 3; ++d) sincos(P.p_freq[t][d] * M_PI * X[d], &sn[d], &cs[d]);
+      for (int d = 0; d < 3; ++d) {
+        sn[d] = Pt[t][d][qi[d]][0];
+        cs[d] = Pt[t][d][qi[d]][1];
+      }
       const double A = P.p_amp[t];
       gp[0] += -A * P.p_freq[t][0] * M_PI * sn[0] * cs[1] * cs[2];
       gp[1] += -A * P.p_freq[t][1] * M_PI * cs[0] * sn[1] * cs[2];

@@ -81,12 +81,14 @@ struct PatchArgs {
   T cg_tol;
 };
 
+// Block-wide sums with one barrier: callers alternate between two red
+// buffers, so the previous reads of a buffer are always separated from its
+// next writes by at least one barrier.
 template <typename T, int NW>
 __device__ __forceinline__ T block_sum(T v, T* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
   T s = T(0);
@@ -104,7 +106,6 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
     b += __shfl_xor_sync(0xffffffffu, b, o);
   }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
   if (l == 0) {
     red[w] = a;
     red[NW + w] = b;
@@ -498,7 +499,9 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
   using C = PatchCfg<K>;
   constexpr int BX = C::BX, BOX = C::BOX, NPD = C::NPD;
   __shared__ PatchTables<T> tb;
-  __shared__ T red[2 * C::NW];
+  __shared__ T red[3 * C::NW];
+  T* red_a = red;          // single sums
+  T* red_b = red + C::NW;  // the second single sum of the setup, the pair sums of the CG
   extern __shared__ __align__(16) unsigned char patch_smem[];
   T* Ft = reinterpret_cast<T*>(patch_smem);  // 3 boxes: S^T F, kept to the end
   T* Ba = Ft + 3 * BOX;                      // 3 boxes of work space
@@ -586,7 +589,7 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
     R[o] = r;
     s1 += r;
   }
-  T mean = block_sum<T, C::NW>(s1, red) / T(C::NP);
+  T mean = block_sum<T, C::NW>(s1, red_a) / T(C::NP);
   s2 = T(0);
   for (int q = tid; q < C::NP; q += C::NT) {
     const int o = (q % NPD) + BX * (q / NPD);
@@ -596,7 +599,7 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
     Pp[o] = T(0);
     s2 += r * r;
   }
-  T rr = block_sum<T, C::NW>(s2, red);
+  T rr = block_sum<T, C::NW>(s2, red_b);
   const T rr0 = rr;
 
   // ---- conjugate gradients on the mean-free pressures
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
       SD[o] = s;
       part += Dd[o] * s;
     }
-    const T dSd = block_sum<T, C::NW>(part, red);
+    const T dSd = block_sum<T, C::NW>(part, red_a);
     if (!(dSd > T(0))) break;
     const T alpha = rr / dSd;
     s1 = T(0);
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
       s1 += r;
       s2 += r * r;
     }
-    block_sum2<T, C::NW>(s1, s2, red);
+    block_sum2<T, C::NW>(s1, s2, red_b);
     mean = s1 / T(C::NP);
     T rr_new = s2 - s1 * mean;  // sum (r - mean)^2
     if (rr_new < T(0)) rr_new = T(0);
