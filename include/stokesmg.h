@@ -146,15 +146,20 @@ int stk_smooth(stk_problem* P, int level, int dtype, void* x, const void* b);
 
 /* x = A_0^+ b on level 0 (the exact coarse solve P_0^{-1} = A_0^{-1} of
  * Sec. 3; the pressure null space is removed: the result is the
- * pseudo-inverse with mean-free pressure coefficients).  Needs a 2^3 coarse
- * mesh (n = 2^L); the first call builds the dense FP64 pseudo-inverse on the
- * GPU (one exact patch solve per coarse DoF) and is synchronous. */
+ * pseudo-inverse with mean-free pressure coefficients), always computed in
+ * FP64.  On a 2^3 coarse mesh (n = 2^L) the first call builds the dense
+ * pseudo-inverse (one exact patch solve per coarse DoF); on a 3^3 mesh
+ * (n = 3 * 2^L) it builds dense inverses of the three velocity blocks and of
+ * the pressure Schur complement (shared by every problem of the process with
+ * the same device, degree, viscosity and penalty factor) and solves by block
+ * elimination.  The first call is synchronous. */
 int stk_coarse_solve(stk_problem* P, int dtype, const void* b, void* x);
 
 /* x = P_L^{-1} b on the finest level: one V-cycle with x0 = 0, one pre- and
  * one post-smoothing step, residual restriction, exact coarse solve and
  * prolongation (Sec. 3).  Every level runs in dtype; the coarse solve always
- * accumulates in FP64.  Needs n = 2^L.  b and x must not alias. */
+ * runs in FP64.  The hierarchy ends on 2^3 (n = 2^L) or 3^3 (n = 3 * 2^L)
+ * cells.  b and x must not alias. */
 int stk_vcycle(stk_problem* P, int dtype, const void* b, void* x);
 
 /* Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 by flexible GMRES(restart)
@@ -169,12 +174,12 @@ int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve
 
 /* Solve `count` independent problems (each with its own setup, mesh, degree
  * and options) to ||b_i - A_i x_i|| <= rtol ||b_i||, by the same method as
- * stk_solve.  The host interleaves the solves: every round it enqueues one
- * step of each unfinished solve on that problem's stream, then waits for each
- * stream and advances its Krylov state, so problems on distinct non-NULL
- * streams run concurrently on the GPU (many small problems fill the GPU that
- * one alone cannot; the mixed-precision V-cycles replay captured CUDA
- * graphs).  b[i], x[i]: FP64 device vectors of problem i's finest level.
+ * stk_solve, with bitwise the same results.  The host interleaves the
+ * solves: it polls the problems' streams and, as soon as one has drained,
+ * advances that problem's Krylov state and enqueues its next step, so
+ * problems on distinct non-NULL streams run concurrently on the GPU (many
+ * small problems fill the GPU that one alone cannot; the V-cycles replay
+ * captured CUDA graphs).  b[i], x[i]: FP64 device vectors of problem i's finest level.
  * infos may be NULL, else count entries.  Synchronous.  Returns STK_OK,
  * STK_ENOCONV if any solve reached its max_iter, or the first other error;
  * stk_last_error(NULL) names the failing problem.  No problem may appear
