@@ -144,6 +144,20 @@ int stk_restrict(stk_problem* P, int fine_level, int dtype, const void* rf, void
  * allocates that dtype's multigrid workspace (three vectors per level). */
 int stk_smooth(stk_problem* P, int level, int dtype, void* x, const void* b);
 
+/* One smoothing step (as stk_smooth) of `count` problems of the same degree
+ * k, batched (the patch launches are not in the paper, which smooths one
+ * problem): per colour, every problem's colour residual, then ONE launch of
+ * the patch kernel over that colour's patches of all the problems (64
+ * problems per launch).  levels[i]: the level smoothed in problem i; x[i],
+ * b[i]: its vectors, as in stk_smooth.  All work runs on problems[0]'s
+ * stream, whose caller orders the other problems' streams before the call;
+ * the local-solver options of problems[0] apply to all.  The result equals
+ * `count` separate stk_smooth calls bitwise.  Errors: STK_EINVAL for NULL or
+ * empty arguments, mixed degrees, a repeated problem, aliasing x[i] and b[i]
+ * (stk_last_error(NULL) says which); nothing is launched then. */
+int stk_smooth_batch(stk_problem* const* problems, int count, const int* levels, int dtype, void* const* x,
+                     const void* const* b);
+
 /* x = A_0^+ b on level 0 (the exact coarse solve P_0^{-1} = A_0^{-1} of
  * Sec. 3; the pressure null space is removed: the result is the
  * pseudo-inverse with mean-free pressure coefficients), always computed in

@@ -92,6 +92,7 @@ def load_library():
         "stk_autotune": (ctypes.c_int, [P, ctypes.c_int]),
         "stk_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
+        "stk_smooth_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -284,6 +285,24 @@ class StokesMG:
         n = info.iterations
         return {"iterations": n, "converged": bool(info.converged), "relres": info.relres, "nu": info.nu,
                 "seconds": info.seconds, "residuals": list(info.residuals[: min(n, 255) + 1]), "status": rc}
+
+
+def smooth_batch(problems, xs, bs, levels=None):
+    """One smoothing step of several problems of the same degree (stk_smooth_batch),
+    on problems[0]'s stream; levels default to every problem's finest level."""
+    lib = load_library()
+    n = len(problems)
+    if levels is None:
+        levels = [p.num_levels - 1 for p in problems]
+    dt = problems[0]._dt(xs[0])
+    P = ctypes.c_void_p
+    hs = (P * n)(*[p.h for p in problems])
+    lv = (ctypes.c_int * n)(*[p._lvl(l) for p, l in zip(problems, levels)])
+    xp = (P * n)(*[p._vec(x, p._lvl(l), dt) for p, x, l in zip(problems, xs, levels)])
+    bp = (P * n)(*[p._vec(b, p._lvl(l), dt) for p, b, l in zip(problems, bs, levels)])
+    rc = lib.stk_smooth_batch(hs, n, lv, dt, xp, bp)
+    if rc != 0:
+        raise StokesError(rc, lib.stk_last_error(None).decode())
 
 
 def solve_batch(problems, bs, xs, rtol: float = 1e-8):

@@ -281,6 +281,29 @@ int stk_smooth(stk_problem* P, int level, int dtype, void* x, const void* b) {
   return status_of(P, stk::run_smooth(P, level, dtype, x, b), "smooth");
 }
 
+int stk_smooth_batch(stk_problem* const* problems, int count, const int* levels, int dtype, void* const* x,
+                     const void* const* b) {
+  if (!problems || count < 1 || !levels || !x || !b) return fail(nullptr, STK_EINVAL, "smooth_batch: empty or NULL arguments");
+  if (dtype != STK_F64 && dtype != STK_F32) return fail(nullptr, STK_EINVAL, "dtype must be STK_F64 or STK_F32");
+  for (int i = 0; i < count; ++i) {
+    stk_problem* P = problems[i];
+    if (!P) return fail(nullptr, STK_EINVAL, "smooth_batch: NULL problem");
+    if (P->k != problems[0]->k) return fail(nullptr, STK_EINVAL, "smooth_batch: problems of different degrees");
+    int rc;
+    if ((rc = check_level(P, levels[i])) || (rc = check_vec(P, x[i], "x")) || (rc = check_vec(P, b[i], "b"))) {
+      g_setup_error = "problem " + std::to_string(i) + ": " + P->err;
+      return rc;
+    }
+    if (x[i] == b[i]) return fail(nullptr, STK_EINVAL, "smooth_batch: x and b must not alias");
+    for (int j = 0; j < i; ++j)
+      if (problems[j] == P) return fail(nullptr, STK_EINVAL, "smooth_batch: a problem appears twice");
+  }
+  const cudaError_t e = stk::run_smooth_batch(problems, levels, count, dtype, x, b);
+  if (e != cudaSuccess) return fail(nullptr, e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA,
+                                    std::string("smooth_batch: ") + cudaGetErrorString(e));
+  return STK_OK;
+}
+
 int stk_coarse_solve(stk_problem* P, int dtype, const void* b, void* x) {
   if (!P) return STK_EINVAL;
   int rc;

@@ -421,14 +421,19 @@ static cudaError_t dispatch_apply(int k, const Level& L, const CellTables<T>& ta
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_apply(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
-                         double alpha, int stages) {
+cudaError_t launch_apply_on(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
+                            double alpha, int stages, cudaStream_t stream) {
   const Level& L = P->levels[level];
   if (dtype == STK_F64)
     return dispatch_apply<double>(P->k, L, L.htab64, (const double*)x, (const double*)b, (double*)y, alpha, stages,
-                                  P->stream);
+                                  stream);
   return dispatch_apply<float>(P->k, L, L.htab32, (const float*)x, (const float*)b, (float*)y, (float)alpha, stages,
-                               P->stream);
+                               stream);
+}
+
+cudaError_t launch_apply(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
+                         double alpha, int stages) {
+  return launch_apply_on(P, level, dtype, x, b, y, alpha, stages, P->stream);
 }
 
 }  // namespace stk

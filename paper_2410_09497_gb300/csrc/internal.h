@@ -48,6 +48,7 @@ struct Tables1D {
   std::vector<double> S;
 };
 
+constexpr int kMaxPatchJobs = 64;  // problems per multi-problem patch launch
 constexpr int kMaxPC = 2 * kMaxDegree + 1;  // patch-interior nodes, continuous direction
 constexpr int kMaxPD = 2 * kMaxDegree + 2;  // patch nodes, discontinuous direction
 
@@ -169,6 +170,9 @@ namespace stk {
 // stages: bit 0 = velocity rows, bit 1 = pressure rows (3 = the whole operator).
 cudaError_t launch_apply(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
                          double alpha, int stages = 3);
+// the same on a given stream
+cudaError_t launch_apply_on(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
+                            double alpha, int stages, cudaStream_t stream);
 // xf += I^up xc (xc on fine_level - 1); rc = I^down rf (rc is overwritten).
 cudaError_t launch_prolongate_add(const stk_problem* P, int fine_level, int dtype, const void* xc, void* xf);
 cudaError_t launch_restrict(const stk_problem* P, int fine_level, int dtype, const void* rf, void* rc);
@@ -178,6 +182,10 @@ cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int 
 cudaError_t launch_patch_colour_cg(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x,
                                    int cg_tol_mode, int cg_iters, double cg_tol);
 cudaError_t launch_coarse_columns(const stk_problem* P, double* cols, int max_iter, double tol);
+// one colour of `count` problems of the same degree (levels[i] of problem i),
+// kMaxPatchJobs problems per launch, on `stream`; local-solver options of Ps[0]
+cudaError_t launch_patch_colour_multi(const stk_problem* const* Ps, const int* levels, int count, int dtype,
+                                      int colour, void* const* r, void* const* x, cudaStream_t stream);
 cudaError_t launch_coarse_solve(const stk_problem* P, int dtype, const void* b, void* x);
 // coarse3.cu: exact solve on a 3^3 coarse mesh.  acquire_coarse3 builds (or
 // takes from the cache) the dense factors, using P->coarse3 as probes and
@@ -189,6 +197,8 @@ cudaError_t coarse3_solve(stk_problem* P);
 cudaError_t ensure_mg_workspace(stk_problem* P, int dtype);
 cudaError_t ensure_coarse(stk_problem* P);
 cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void* b);
+cudaError_t run_smooth_batch(stk_problem* const* Ps, const int* levels, int count, int dtype, void* const* x,
+                             const void* const* b);
 cudaError_t run_vcycle(stk_problem* P, int dtype, const void* b, void* x);
 cudaError_t run_coarse_solve(stk_problem* P, int dtype, const void* b, void* x);
 int run_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info, std::string& err);

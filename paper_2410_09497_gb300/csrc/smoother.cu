@@ -84,6 +84,18 @@ struct PatchArgs {
 // Block-wide sums with one barrier: callers alternate between two red
 // buffers, so the previous reads of a buffer are always separated from its
 // next writes by at least one barrier.
+// Per-problem fields of a multi-problem colour launch (passed by value).
+template <typename T>
+struct PatchJobs {
+  int count;
+  int first[kMaxPatchJobs];  // first CTA of each problem
+  const T* r[kMaxPatchJobs];
+  T* x[kMaxPatchJobs];
+  const PatchTables<T>* tab[kMaxPatchJobs];
+  int n[kMaxPatchJobs], m[kMaxPatchJobs];
+  int cnt[kMaxPatchJobs][3];
+};
+
 template <typename T, int NW>
 __device__ __forceinline__ T block_sum(T v, T* red) {
 #pragma unroll
@@ -494,8 +506,10 @@ __device__ __forceinline__ int64_t patch_global(int j, const int* v, int m) {
   return patch_node_global<K>(c, i0, i1, i2, v, m);
 }
 
+// Gather, local solve and scatter of patch `blk` of the colour (mode 0) or of
+// coarse column `blk` (mode 1); the body of both patch kernels below.
 template <int K, typename T>
-__global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patch_kernel(PatchArgs<T> A) {
+__device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk) {
   using C = PatchCfg<K>;
   constexpr int BX = C::BX, BOX = C::BOX, NPD = C::NPD;
   __shared__ PatchTables<T> tb;
@@ -529,7 +543,7 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
 
   int v[3];
   if (A.mode == 0) {
-    int p = blockIdx.x;
+    int p = blk;
     for (int d = 0; d < 3; ++d) {
       const int t = p % A.cnt[d];
       p /= A.cnt[d];
@@ -560,7 +574,7 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
         if (A.mode == 0)
           val[u] = A.r[patch_node_global<K>(c, i0, i1, i2, v, A.m)];
         else
-          val[u] = (j == (int)blockIdx.x) ? T(1) : T(0);
+          val[u] = (j == blk) ? T(1) : T(0);
       }
     }
 #pragma unroll
@@ -679,7 +693,7 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
         patch_local_decode<K>(j, c, i0, i1, i2);
         const int o = i0 + BX * (i1 + NPD * i2);
         val[u] = (c < 3) ? Bb[c * BOX + o] : Pp[o];
-        gi[u] = A.mode == 0 ? patch_node_global<K>(c, i0, i1, i2, v, A.m) : (int64_t)blockIdx.x * NL + j;
+        gi[u] = A.mode == 0 ? patch_node_global<K>(c, i0, i1, i2, v, A.m) : (int64_t)blk * NL + j;
       }
     }
     if (A.mode == 0) {
@@ -695,6 +709,35 @@ __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patc
         if (gi[u] >= 0) A.cols[gi[u]] = (double)val[u];
     }
   }
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patch_kernel(PatchArgs<T> A) {
+  patch_solve<K, T>(A, blockIdx.x);
+}
+
+// One colour of several problems of the same degree in one launch: CTA b
+// solves patch b - first[j] of problem j (first[] ascending); the per-problem
+// fields replace those of the common arguments.
+template <int K, typename T>
+__global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value))
+    patch_kernel_multi(PatchArgs<T> A, PatchJobs<T> J) {
+  int lo = 0, hi = J.count - 1;  // last job with first[job] <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (J.first[mid] <= (int)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  PatchArgs<T> a = A;
+  a.r = J.r[lo];
+  a.x = J.x[lo];
+  a.tab = J.tab[lo];
+  a.n = J.n[lo];
+  a.m = J.m[lo];
+  for (int d = 0; d < 3; ++d) a.cnt[d] = J.cnt[lo][d];
+  patch_solve<K, T>(a, (int)blockIdx.x - J.first[lo]);
 }
 
 template <int K>
@@ -724,6 +767,33 @@ static cudaError_t dispatch_patch(int k, PatchArgs<T> a, int nblocks, cudaStream
     case 3: return launch_patch_k<3, T>(a, nblocks, s);
     case 4: return launch_patch_k<4, T>(a, nblocks, s);
     case 5: return launch_patch_k<5, T>(a, nblocks, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int K, typename T>
+static cudaError_t launch_patch_multi_k(const PatchArgs<T>& a, const PatchJobs<T>& J, int nblocks, cudaStream_t s) {
+  using C = PatchCfg<K>;
+  const size_t smem = patch_smem_bytes<K>(sizeof(T));
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(patch_kernel_multi<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (nblocks > 0) patch_kernel_multi<K, T><<<nblocks, C::NT, smem, s>>>(a, J);
+  return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t dispatch_patch_multi(int k, const PatchArgs<T>& a, const PatchJobs<T>& J, int nblocks,
+                                        cudaStream_t s) {
+  switch (k) {
+    case 1: return launch_patch_multi_k<1, T>(a, J, nblocks, s);
+    case 2: return launch_patch_multi_k<2, T>(a, J, nblocks, s);
+    case 3: return launch_patch_multi_k<3, T>(a, J, nblocks, s);
+    case 4: return launch_patch_multi_k<4, T>(a, J, nblocks, s);
+    case 5: return launch_patch_multi_k<5, T>(a, J, nblocks, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -782,6 +852,50 @@ cudaError_t launch_patch_colour_cg(const stk_problem* P, int level, int dtype, i
 cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x) {
   return launch_patch_colour_cg(P, level, dtype, colour, r, x, P->opt.local_cg_mode == STK_CG_TOL,
                                 P->opt.local_cg_iters, P->opt.local_cg_tol);
+}
+
+template <typename T>
+static cudaError_t patch_colour_multi(const stk_problem* const* Ps, const int* levels, int count, int colour,
+                                      void* const* r, void* const* x, cudaStream_t stream) {
+  for (int i0 = 0; i0 < count; i0 += kMaxPatchJobs) {
+    const int nj = std::min(kMaxPatchJobs, count - i0);
+    PatchArgs<T> a;
+    fill_common(Ps[0], Ps[0]->levels[levels[0]], a);
+    a.r = nullptr;
+    a.x = nullptr;
+    a.tab = nullptr;
+    a.colour = colour;
+    a.mode = 0;
+    PatchJobs<T> J{};
+    J.count = nj;
+    int total = 0;
+    for (int j = 0; j < nj; ++j) {
+      const stk_problem* P = Ps[i0 + j];
+      const Level& L = P->levels[levels[i0 + j]];
+      int cnt[3];
+      colour_counts(L.n, colour, cnt);
+      J.first[j] = total;
+      J.r[j] = (const T*)r[i0 + j];
+      J.x[j] = (T*)x[i0 + j];
+      if constexpr (sizeof(T) == 8)
+        J.tab[j] = L.ptab64;
+      else
+        J.tab[j] = L.ptab32;
+      J.n[j] = L.n;
+      J.m[j] = L.m;
+      for (int d = 0; d < 3; ++d) J.cnt[j][d] = cnt[d];
+      total += cnt[0] * cnt[1] * cnt[2];
+    }
+    cudaError_t e = dispatch_patch_multi<T>(Ps[0]->k, a, J, total, stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_patch_colour_multi(const stk_problem* const* Ps, const int* levels, int count, int dtype,
+                                      int colour, void* const* r, void* const* x, cudaStream_t stream) {
+  if (dtype == STK_F64) return patch_colour_multi<double>(Ps, levels, count, colour, r, x, stream);
+  return patch_colour_multi<float>(Ps, levels, count, colour, r, x, stream);
 }
 
 int patch_local_size(int k) {

@@ -201,6 +201,29 @@ cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void
   return cudaSuccess;
 }
 
+// One smoothing step of several problems of the same degree, all on the first
+// problem's stream: per colour, every problem's colour residual, then one
+// patch launch over the colour's patches of all of them.
+cudaError_t run_smooth_batch(stk_problem* const* Ps, const int* levels, int count, int dtype, void* const* x,
+                             const void* const* b) {
+  const cudaStream_t s = Ps[0]->stream;
+  std::vector<void*> r(count);
+  for (int i = 0; i < count; ++i) {
+    cudaError_t e = ensure_mg_workspace(Ps[i], dtype);
+    if (e != cudaSuccess) return e;
+    r[i] = Ps[i]->mg[dtype].r[levels[i]];
+  }
+  for (int colour = 0; colour < 8; ++colour) {
+    for (int i = 0; i < count; ++i) {
+      cudaError_t e = launch_apply_on(Ps[i], levels[i], dtype, x[i], b[i], r[i], -1.0, 3, s);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_patch_colour_multi(Ps, levels, count, dtype, colour, r.data(), x, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Coarse solve P_0^{-1} (Sec. 3), exact in FP64 whatever the V-cycle's
 // precision.  On the 2^3 mesh: the dense pseudo-inverse.  On a 3^3 mesh
 // (n = 3 * 2^L): block elimination with dense factors of the velocity blocks

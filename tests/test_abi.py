@@ -48,6 +48,10 @@ def test_invalid_arguments_fail_without_gpu(lib):
     assert lib.stk_setup(10, 2, 1.0, None, ctypes.byref(P)) == -1  # not 2 or 3 times a power of two
     assert lib.stk_setup(8, 2, -1.0, None, ctypes.byref(P)) == -1  # viscosity
     assert lib.stk_destroy(None) == 0
+    # batched entry points reject empty or NULL arguments before touching a device
+    assert lib.stk_smooth_batch(None, 0, None, 0, None, None) == -1
+    assert b"smooth_batch" in lib.stk_last_error(None)
+    assert lib.stk_solve_batch(None, 0, None, None, ctypes.c_double(1e-8), None) == -1
 
 
 def test_binding_layout_matches_oracle_numbering():

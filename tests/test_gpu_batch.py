@@ -91,3 +91,35 @@ def test_graph_replay_equals_direct_launches(stk):
         out.append(x.cpu().numpy())
         P.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("dtype_name", ["f64", "f32"])
+def test_smooth_batch_equals_separate_smoothing(stk, dtype_name):
+    """One smoothing step of several problems of the same degree with one patch
+    launch per colour equals separate smoothing steps bitwise, on the finest
+    and on coarser levels."""
+    import torch
+
+    from seeded_inputs import random_vector
+
+    dt = torch.float64 if dtype_name == "f64" else torch.float32
+    sizes = [(4, -1), (6, -1), (8, -1), (3, -1), (8, 1), (12, 1)]
+    s = torch.cuda.Stream()
+    probs = [stk.StokesMG(n, 2, 1.0, stream=s) for n, _ in sizes]
+    levels = [P._lvl(l) for P, (_, l) in zip(probs, sizes)]
+    xs, bs = [], []
+    for i, (P, l) in enumerate(zip(probs, levels)):
+        N = P.layout(l)["n_total"]
+        xs.append(torch.from_numpy(random_vector(700 + i, N)).to(dt).cuda())
+        bs.append(torch.from_numpy(random_vector(800 + i, N)).to(dt).cuda())
+    ref = [x.clone() for x in xs]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for P, x, b, l in zip(probs, ref, bs, levels):
+            P.smooth(x, b, level=l)
+        stk.smooth_batch(probs, xs, bs, levels)
+    s.synchronize()
+    for a, r in zip(xs, ref):
+        assert torch.equal(a, r)
+    for P in probs:
+        P.close()
