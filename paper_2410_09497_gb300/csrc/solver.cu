@@ -237,7 +237,7 @@ __global__ void copy_convert_kernel(const S* __restrict__ src, D* __restrict__ d
 
 // Remove the mean of the pressure rows (one CTA; the coarse pressure block is
 // small): the bordered coarse system maps the right-hand side's pressure
-// mean to its multiplier, so the sweeps work on the consistent part only.
+// mean to its multiplier, so the block elimination sees a consistent system.
 __global__ void __launch_bounds__(256) remove_pressure_sum(double* __restrict__ p, int64_t np) {
   __shared__ double red[8];
   double s = 0.0;
