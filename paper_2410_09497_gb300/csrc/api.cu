@@ -162,10 +162,10 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
     stk::PatchTables<float> p32;
     stk::fill_patch_tables(pt, &p64);
     stk::fill_patch_tables(pt, &p32);
-    cudaError_t e = cudaMalloc(&L.tab64, sizeof(h64));
-    if (e == cudaSuccess) e = cudaMalloc(&L.tab32, sizeof(h32));
-    if (e == cudaSuccess) e = cudaMalloc(&L.ptab64, sizeof(p64));
-    if (e == cudaSuccess) e = cudaMalloc(&L.ptab32, sizeof(p32));
+    cudaError_t e = stk::dev_alloc(&L.tab64, sizeof(h64));
+    if (e == cudaSuccess) e = stk::dev_alloc(&L.tab32, sizeof(h32));
+    if (e == cudaSuccess) e = stk::dev_alloc(&L.ptab64, sizeof(p64));
+    if (e == cudaSuccess) e = stk::dev_alloc(&L.ptab32, sizeof(p32));
     if (e == cudaSuccess) e = cudaMemcpy(L.tab64, &h64, sizeof(h64), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L.tab32, &h32, sizeof(h32), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L.ptab64, &p64, sizeof(p64), cudaMemcpyHostToDevice);
@@ -180,9 +180,9 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
     const std::vector<double> xt = stk::build_transfer_tables(k);
     std::vector<float> xt32(xt.begin(), xt.end());
     const std::vector<double>& S = P->levels.back().t1d.S;
-    cudaError_t e = cudaMalloc(&P->xfer64, sizeof(double) * xt.size());
-    if (e == cudaSuccess) e = cudaMalloc(&P->xfer32, sizeof(float) * xt.size());
-    if (e == cudaSuccess) e = cudaMalloc(&P->pmean_w, sizeof(double) * S.size());
+    cudaError_t e = stk::dev_alloc(&P->xfer64, sizeof(double) * xt.size());
+    if (e == cudaSuccess) e = stk::dev_alloc(&P->xfer32, sizeof(float) * xt.size());
+    if (e == cudaSuccess) e = stk::dev_alloc(&P->pmean_w, sizeof(double) * S.size());
     if (e == cudaSuccess) e = cudaMemcpy(P->xfer64, xt.data(), sizeof(double) * xt.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->xfer32, xt32.data(), sizeof(float) * xt.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->pmean_w, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice);
@@ -366,8 +366,8 @@ int stk_autotune(stk_problem* P, int dtype) {
   for (size_t l = 0; e == cudaSuccess && l < P->levels.size(); ++l) {
     stk::Level& L = P->levels[l];
     void *x = nullptr, *y = nullptr;
-    e = cudaMalloc(&x, L.ntotal * es);
-    if (e == cudaSuccess) e = cudaMalloc(&y, L.ntotal * es);
+    e = stk::dev_alloc(&x, L.ntotal * es);
+    if (e == cudaSuccess) e = stk::dev_alloc(&y, L.ntotal * es);
     if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, L.ntotal * es, P->stream);
     float best = 1e30f;
     int best_chunk = 0;

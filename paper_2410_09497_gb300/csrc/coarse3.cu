@@ -239,7 +239,7 @@ cudaError_t gemv(const double* M, int64_t n, int64_t ld, int nmat, const double*
 // In-place Gauss-Jordan inverse of nmat matrices (n x n, stride ld).
 cudaError_t gauss_jordan(double* M, int64_t n, int64_t ld, int nmat, cudaStream_t s) {
   double* buf = nullptr;
-  cudaError_t e = cudaMallocAsync(&buf, sizeof(double) * 4 * (size_t)nmat * ld, s);
+  cudaError_t e = dev_alloc_async(&buf, sizeof(double) * 4 * (size_t)nmat * ld, s);
   if (e != cudaSuccess) return e;
   gj_init<<<dim3((unsigned)((n + 255) / 256), nmat), 256, 0, s>>>(M, n, ld, nmat, buf);
   const dim3 grid((unsigned)((n + kGjRows - 1) / kGjRows), nmat);
@@ -273,6 +273,8 @@ uint64_t bits(double v) {
   return b;
 }
 
+cudaError_t fill_factors(stk_problem* P, Coarse3Factors& F, unsigned char* flag);
+
 // Builds the factors on the problem's stream with its coarse FP64 vectors
 // (x = coarse3[1], y = coarse3[2]) as probes; synchronizes at the end.
 cudaError_t build_factors(stk_problem* P, Coarse3Factors& F) {
@@ -283,13 +285,28 @@ cudaError_t build_factors(stk_problem* P, Coarse3Factors& F) {
   F.np = np;
   F.ldA = round_ld(nc);
   F.ldS = round_ld(np);
-  cudaError_t e = cudaMalloc(&F.Ainv, sizeof(double) * 3 * (size_t)nc * F.ldA);
-  if (e == cudaSuccess) e = cudaMalloc(&F.Sinv, sizeof(double) * (size_t)np * F.ldS);
+  cudaError_t e = dev_alloc(&F.Ainv, sizeof(double) * 3 * (size_t)nc * F.ldA);
+  if (e == cudaSuccess) e = dev_alloc(&F.Sinv, sizeof(double) * (size_t)np * F.ldS);
   if (e != cudaSuccess) return e;
-  double *x = P->coarse3[1], *y = P->coarse3[2], *t = P->coarse3[0];
   unsigned char* flag = nullptr;
-  e = cudaMallocAsync(&flag, 3 * (size_t)nc, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(F.Ainv, 0, sizeof(double) * 3 * (size_t)nc * F.ldA, s);
+  e = dev_alloc_async(&flag, 3 * (size_t)nc, s);
+  if (e != cudaSuccess) return e;
+  e = fill_factors(P, F, flag);
+  const cudaError_t e2 = cudaFreeAsync(flag, s);  // on every path
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+// The probes, eliminations and shift of build_factors; flag: 3 n_c bytes of
+// device scratch.
+cudaError_t fill_factors(stk_problem* P, Coarse3Factors& F, unsigned char* flag) {
+  const Level& L = P->levels[0];
+  const cudaStream_t s = P->stream;
+  const int64_t nc = L.nvel, np = L.npress, N = L.ntotal;
+  double *x = P->coarse3[1], *y = P->coarse3[2], *t = P->coarse3[0];
+  cudaError_t e = cudaMemsetAsync(F.Ainv, 0, sizeof(double) * 3 * (size_t)nc * F.ldA, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(F.Sinv, 0, sizeof(double) * (size_t)np * F.ldS, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(double) * N, s);
   if (e != cudaSuccess) return e;
@@ -321,12 +338,7 @@ cudaError_t build_factors(stk_problem* P, Coarse3Factors& F) {
   double* alpha = reinterpret_cast<double*>(flag);  // 3 nc >= 8 bytes, flags no longer needed
   schur_shift<<<1, 256, 0, s>>>(F.Sinv, np, F.ldS, alpha);
   add_shift<<<(unsigned)std::min<int64_t>((np * np + 255) / 256, 4096), 256, 0, s>>>(F.Sinv, np, F.ldS, alpha);
-  e = gauss_jordan(F.Sinv, np, F.ldS, 1, s);
-  cudaError_t e2 = cudaFreeAsync(flag, s);
-  if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return e;
+  return gauss_jordan(F.Sinv, np, F.ldS, 1, s);
 }
 
 }  // namespace

@@ -12,6 +12,23 @@
 
 namespace stk {
 
+// alloc.cu: all allocations of the library (with the host-side fault injector)
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t dev_alloc_async(void** p, size_t bytes, cudaStream_t s);
+cudaError_t host_alloc_pinned(void** p, size_t bytes);
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc(reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+cudaError_t dev_alloc_async(T** p, size_t bytes, cudaStream_t s) {
+  return dev_alloc_async(reinterpret_cast<void**>(p), bytes, s);
+}
+template <typename T>
+cudaError_t host_alloc_pinned(T** p, size_t bytes) {
+  return host_alloc_pinned(reinterpret_cast<void**>(p), bytes);
+}
+
 constexpr int kMaxDegree = 5;
 constexpr int kMaxC = kMaxDegree + 2;  // nodes of a cell in the continuous direction
 constexpr int kMaxD = kMaxDegree + 1;  // nodes of a cell in a discontinuous direction

@@ -144,8 +144,16 @@ __global__ void pressure_shift(double* __restrict__ p, int64_t np, const double*
 static int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 8); }
 
 // --------------------------------------------------------------- workspace
-static cudaError_t dmalloc(void** p, size_t bytes) { return cudaMalloc(p, bytes); }
+static void free_all(std::vector<void*>& v) {
+  for (void*& p : v)
+    if (p) {
+      cudaFree(p);
+      p = nullptr;
+    }
+}
 
+// A failed allocation leaves the workspace empty (nothing leaks, a later
+// call starts over).
 cudaError_t ensure_mg_workspace(stk_problem* P, int dtype) {
   MgWork& W = P->mg[dtype];
   if (W.ready) return cudaSuccess;
@@ -156,10 +164,15 @@ cudaError_t ensure_mg_workspace(stk_problem* P, int dtype) {
   W.x.assign(nl, nullptr);
   for (int l = 0; l < nl; ++l) {
     const size_t bytes = (size_t)P->levels[l].ntotal * es;
-    cudaError_t e = dmalloc(&W.r[l], bytes);
-    if (e == cudaSuccess) e = dmalloc(&W.b[l], bytes);
-    if (e == cudaSuccess) e = dmalloc(&W.x[l], bytes);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = dev_alloc(&W.r[l], bytes);
+    if (e == cudaSuccess) e = dev_alloc(&W.b[l], bytes);
+    if (e == cudaSuccess) e = dev_alloc(&W.x[l], bytes);
+    if (e != cudaSuccess) {
+      free_all(W.r);
+      free_all(W.b);
+      free_all(W.x);
+      return e;
+    }
   }
   W.ready = true;
   return cudaSuccess;
@@ -172,19 +185,23 @@ cudaError_t ensure_coarse(stk_problem* P) {
     const size_t bytes = sizeof(double) * (size_t)P->levels[0].ntotal;
     for (int i = 0; i < 3; ++i) {
       if (P->coarse3[i]) continue;
-      cudaError_t e = cudaMalloc(&P->coarse3[i], bytes);
+      cudaError_t e = dev_alloc(&P->coarse3[i], bytes);
       if (e != cudaSuccess) return e;
     }
     return acquire_coarse3(P);
   }
   if (P->coarse_inv) return cudaSuccess;
   const int NL = patch_local_size(P->k);
-  cudaError_t e = cudaMalloc(&P->coarse_inv, sizeof(double) * (size_t)NL * NL);
+  cudaError_t e = dev_alloc(&P->coarse_inv, sizeof(double) * (size_t)NL * NL);
   if (e != cudaSuccess) return e;
   // every free coarse DoF's pseudo-inverse column: CG on the Schur complement to 1e-14
   e = launch_coarse_columns(P, P->coarse_inv, 2000, 1e-14);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) {  // no half-built inverse survives a failure
+    cudaFree(P->coarse_inv);
+    P->coarse_inv = nullptr;
+  }
+  return e;
 }
 
 // ---------------------------------------------------------------- smoother
@@ -304,12 +321,21 @@ cudaError_t ensure_krylov(stk_problem* P) {
   const int m = P->opt.gmres_restart;
   if (K.ready) return cudaSuccess;
   const int64_t n = P->levels.back().ntotal;
-  cudaError_t e = cudaMalloc(&K.V, sizeof(double) * (size_t)(m + 1) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&K.Z, sizeof(double) * (size_t)m * n);
-  if (e == cudaSuccess) e = cudaMalloc(&K.partial, sizeof(double) * (size_t)kRedBlocks * kMaxBasis);
-  if (e == cudaSuccess) e = cudaMalloc(&K.h, sizeof(double) * 2 * kMaxBasis);
-  if (e == cudaSuccess) e = cudaMallocHost(&K.h_host, sizeof(double) * 2 * kMaxBasis);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = dev_alloc(&K.V, sizeof(double) * (size_t)(m + 1) * n);
+  if (e == cudaSuccess) e = dev_alloc(&K.Z, sizeof(double) * (size_t)m * n);
+  if (e == cudaSuccess) e = dev_alloc(&K.partial, sizeof(double) * (size_t)kRedBlocks * kMaxBasis);
+  if (e == cudaSuccess) e = dev_alloc(&K.h, sizeof(double) * 2 * kMaxBasis);
+  if (e == cudaSuccess) e = host_alloc_pinned(&K.h_host, sizeof(double) * 2 * kMaxBasis);
+  if (e != cudaSuccess) {  // leave nothing half allocated
+    for (double** d : {&K.V, &K.Z, &K.partial, &K.h})
+      if (*d) {
+        cudaFree(*d);
+        *d = nullptr;
+      }
+    if (K.h_host) cudaFreeHost(K.h_host);
+    K.h_host = nullptr;
+    return e;
+  }
   K.ready = true;
   return cudaSuccess;
 }
