@@ -9,8 +9,9 @@ larger than the 129 MB L2, so no flush is needed between steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-The same JSON line carries sub-benchmarks of the other workloads: `sweep`
-(FP64 apply, 64^3 cells, k = 1..5), `smooth` (one smoothing step, 64^3,
+The same JSON line carries sub-benchmarks of the other workloads:
+`apply_f32` (the FP32 apply of the V-cycle, same mesh), `sweep` (FP64 apply,
+64^3 cells, k = 1..5), `smooth` (one smoothing step, 64^3,
 k = 3, FP32 and FP64), `solve` (manufactured problem on 96^3 cells, k = 3,
 to 1e-8: mixed precision against plain FP64) and `batch` (64 uneven
 problems solved together against one after another); each can be resized or
@@ -358,6 +359,39 @@ def run_sweep(args, stream):
     return out
 
 
+def run_apply_f32(args, stream):
+    """The FP32 apply of the V-cycle on the benchmarked mesh (64^3, k = 3): GDoF/s
+    and the fraction of the HBM roofline (read x, write y: 8 bytes per DoF)."""
+    import torch
+
+    from paper_2410_09497_gb300 import StokesMG, layout_sizes
+    from seeded_inputs import random_vector
+
+    n, k = args.n, args.k
+    nv, npress, N = layout_sizes(n, k)
+    with torch.cuda.stream(stream):
+        P = StokesMG(n, k, 1.0, stream=stream)
+        x = torch.from_numpy(random_vector(1001, N)).float().cuda()
+        y = torch.empty_like(x)
+        for _ in range(3):
+            P.apply(x, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            P.apply(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 20 / 1e3
+        P.close()
+    peaks, src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    flops = velocity_flops_per_dof(k) * 3 * nv + pressure_flops_per_dof(k) * npress
+    return {"workload": f"FP32 Stokes apply, RT_{k} x DGQ_{k}, {n}^3 cells", "gdofs": N / t / 1e9, "ms": t * 1e3,
+            "hbm_gbs": 8 * N / t / 1e9, "frac_hbm": 8 * N / t / 1e9 / hbm, "peak_source": src,
+            "frac_fp32_peak": flops / t / 1e12 / FP32_PEAK_TFLOPS,
+            "l2": "inputs larger than L2 (x and y %d MB each)" % (4 * N // 10**6)}
+
+
 def run_smooth_pair(args, stream):
     """One smoothing step (Algorithm 2: 8 colour residuals and patch solves) in
     FP32 and FP64, ns/DoF (the unit of the paper's smoothing-step row)."""
@@ -585,6 +619,7 @@ def run_ours(args):
         "gpu_launches": 2 * K,
         "clocks": clk.summary(),
     }
+    line["apply_f32"] = run_apply_f32(args, stream)
     if args.sweep_n > 0:
         line["sweep"] = run_sweep(args, stream)
     if args.smooth_n > 0:

@@ -158,6 +158,7 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
     L.htab64 = h64;
     L.htab32 = h32;
     const stk::PatchTables1D pt = stk::build_patch_tables(L.t1d);
+    L.eo_interior = pt.eo_c && pt.eo_d[0];
     stk::PatchTables<double> p64;
     stk::PatchTables<float> p32;
     stk::fill_patch_tables(pt, &p64);

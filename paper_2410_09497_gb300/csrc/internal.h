@@ -142,6 +142,7 @@ struct Level {
   int apply_chunk[2] = {0, 0};          // cells per CTA march of the apply ([dtype]); 0 = default
   PatchTables<double>* ptab64 = nullptr;  // device
   PatchTables<float>* ptab32 = nullptr;   // device
+  bool eo_interior = false;  // continuous and interior 1D eigenbases both in even-odd order
 };
 
 struct MgWork {
