@@ -30,7 +30,9 @@
 //
 // The same kernel, with the right-hand side set to unit vectors, builds the
 // dense pseudo-inverse of the coarse problem at setup: on a 2^3 mesh the one
-// vertex patch holds every free DoF.
+// vertex patch holds every free DoF.  Two more kernels share the patch
+// solve: one for the interior patches of a large level (no dense transforms
+// compiled in) and one for a colour of several problems in one launch.
 #include <algorithm>
 
 #include "internal.h"
