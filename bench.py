@@ -169,14 +169,22 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, v: float) -> float:
+    """The slowest rank's time (NCCL reduces on the GPU, gloo on the host)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ws: int, steps: int, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank runs its own replica of the workload)."""
+    return units_per_rank * ws * steps / seconds
 
 
 def oracle_spmv_rate(n: int, k: int, min_seconds: float, reps_per_step: int = 0):
@@ -588,8 +596,8 @@ def run_ours(args):
         barrier(ws)
         P.close()
 
-    value = N * ws * K / t / 1e9
-    e2e = N * ws * K / t_e2e / 1e9
+    value = whole_job_rate(N, ws, K, t) / 1e9
+    e2e = whole_job_rate(N, ws, K, t_e2e) / 1e9
     peaks, peak_src = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     vflops = velocity_flops_per_dof(k) * 3 * nv
