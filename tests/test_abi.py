@@ -61,3 +61,46 @@ def test_binding_layout_matches_oracle_numbering():
     for n, k in [(2, 1), (6, 3), (64, 3)]:
         d = Discretization(n, k)
         assert layout_sizes(n, k) == (d.n_vel_component, d.n_pressure, d.N)
+
+
+def _build_c_program(tmp_path):
+    import shutil
+    import subprocess
+
+    from paper_2410_09497_gb300 import build
+
+    lib = build.build()
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "c_abi_check")
+    libdir = os.path.dirname(lib)
+    cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "c_abi_check.c"), "-o", exe, "-L", libdir, "-lstokesmg",
+           "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_c_program_against_the_header(tmp_path):
+    """The header compiles as strict C99 and a C program linked to the library
+    gets status codes and messages back without a GPU."""
+    import subprocess
+
+    exe = _build_c_program(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0 and "c abi ok" in r.stdout, (r.returncode, r.stdout, r.stderr)
+
+
+@pytest.mark.gpu
+def test_c_program_sets_up_a_problem(tmp_path):
+    import subprocess
+
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    exe = _build_c_program(tmp_path)
+    r = subprocess.run([exe, "gpu"], capture_output=True, text=True)
+    assert r.returncode == 0 and "layout n=4" in r.stdout, (r.returncode, r.stdout, r.stderr)

@@ -57,7 +57,7 @@ def test_transfers(stk, k, nf):
     P.close()
 
 
-@pytest.mark.parametrize("n,k,iters", [(4, 1, 15), (4, 2, 15), (6, 2, 15), (4, 3, 15), (4, 4, 8), (8, 2, 5)])
+@pytest.mark.parametrize("n,k,iters", [(4, 1, 15), (4, 2, 15), (6, 2, 15), (4, 3, 15), (4, 4, 8), (8, 2, 5), (4, 5, 8)])
 def test_smooth_fixed_cg_matches_oracle(stk, n, k, iters):
     H = Hierarchy(n, k, local=("schur", iters))
     d = H.levels[-1].disc
