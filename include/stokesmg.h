@@ -64,7 +64,8 @@ typedef struct stk_options {
   int max_iter;          /* total GMRES iteration limit, default 200                    */
   int local_cg_mode;     /* STK_CG_FIXED (default) or STK_CG_TOL                       */
   int local_cg_iters;    /* CG steps in FIXED mode, step limit in TOL mode; default 15 */
-  double local_cg_tol;   /* relative CG residual in TOL mode, default 1e-8              */
+  double local_cg_tol;   /* relative CG residual in TOL mode, default 1e-8; FP32 smoothing
+                          * uses max(local_cg_tol, 1e-6), the accuracy an FP32 CG reaches */
   double penalty_factor; /* gamma = penalty_factor (k+1)(k+2)/h, default 1             */
   void* stream;          /* cudaStream_t used by every call, NULL = default stream     */
   int use_graphs;        /* 1 (default): stk_solve replays its V-cycle as a captured

@@ -827,13 +827,22 @@ static void colour_counts(int n, int colour, int* cnt) {
   }
 }
 
+// An FP32 CG stagnates near 1e-6 relative; below that a TOL-mode local solve
+// would run to its step limit and spoil the smoother.
+constexpr double kMinTolF32 = 1e-6;
+
+template <typename T>
+static T local_tol(double tol) {
+  return (T)(sizeof(T) == 4 ? std::max(tol, kMinTolF32) : tol);
+}
+
 template <typename T>
 static void fill_common(const stk_problem* P, const Level& L, PatchArgs<T>& a) {
   a.n = L.n;
   a.m = L.m;
   a.cg_iters = P->opt.local_cg_iters;
   a.cg_tol_mode = P->opt.local_cg_mode == STK_CG_TOL;
-  a.cg_tol = (T)P->opt.local_cg_tol;
+  a.cg_tol = local_tol<T>(P->opt.local_cg_tol);
   a.cols = nullptr;
   a.part = 0;
   for (int d = 0; d < 3; ++d) a.tlo[d] = a.cint[d] = 0;
@@ -875,7 +884,7 @@ static cudaError_t patch_colour(const stk_problem* P, const Level& L, const Patc
   a.mode = 0;
   a.cg_tol_mode = cg_tol_mode;
   a.cg_iters = cg_iters;
-  a.cg_tol = (T)cg_tol;
+  a.cg_tol = local_tol<T>(cg_tol);
   interior_box(L.n, colour, cnt, a.tlo, a.cint);
   const int ni = a.cint[0] * a.cint[1] * a.cint[2];
   // Interior patches in their own launch (no dense transforms compiled in),

@@ -248,3 +248,21 @@ def test_non_convergence_and_bad_arguments_report_status(stk):
     P.apply(dev(b), y)  # still usable
     assert np.isfinite(y.cpu().numpy()).all()
     P.close()
+
+
+def test_tight_local_tolerance_in_fp32_still_converges(stk):
+    """A TOL-mode local CG tighter than FP32 can reach (1e-10) is floored at
+    1e-6 in the FP32 smoother, so the mixed-precision solve converges as with
+    the default fixed step count."""
+    import torch
+
+    s = torch.cuda.Stream()
+    P = stk.StokesMG(32, 3, 1.0, precision=stk.PREC_MIXED, stream=s, local_cg_mode=stk.CG_TOL,
+                     local_cg_iters=200, local_cg_tol=1e-10)
+    b = torch.empty(P.layout()["n_total"], dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(s):
+        P.rhs(manufactured_coefficients(3000), b)
+    x = torch.zeros_like(b)
+    info = P.solve(b, x, rtol=1e-8)
+    assert info["converged"] and info["iterations"] <= 6
+    P.close()
