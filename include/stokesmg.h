@@ -47,7 +47,8 @@ enum {
   STK_ECUDA = -2,    /* a CUDA call failed (message holds the CUDA error string)          */
   STK_ENOMEM = -3,   /* device or host allocation failed                                 */
   STK_ENOCONV = -4,  /* iteration limit reached before the tolerance                     */
-  STK_ETIMEOUT = -5, /* a bounded device-side wait ran out                               */
+  STK_ETIMEOUT = -5, /* a bounded device-side wait ran out (not returned: no kernel of
+                        this library waits on another kernel or on a flag)              */
   STK_ESTATE = -6    /* call not valid in the current state                              */
 };
 
@@ -86,12 +87,13 @@ typedef struct stk_solve_info {
 /* Fill *opt with the defaults listed above.  Returns STK_EINVAL if opt is NULL. */
 int stk_default_options(stk_options* opt);
 
-/* Build the mesh hierarchy, the 1D tables of every level (Sec. 2.3, Sec. 3.2)
- * and all device workspace, for the unit cube with n cells per side, degree k
- * and viscosity nu (Sec. 2, eq. `model` and eq. `weak_form`).  n must be 2 or
- * 3 times a power of two (n >= 2); k in 1..5; nu > 0.  opt may be NULL
- * (defaults).  On success *out owns device memory until stk_destroy.
- * Synchronous. */
+/* Build the mesh hierarchy and the 1D tables of every level (Sec. 2.3,
+ * Sec. 3.2) for the unit cube with n cells per side, degree k and viscosity
+ * nu (Sec. 2, eq. `model` and eq. `weak_form`).  n must be 2 or 3 times a
+ * power of two (n >= 2); k in 1..5; nu > 0.  opt may be NULL (defaults).  The
+ * multigrid workspace of a dtype, the coarse factors and the Krylov basis are
+ * allocated by the first call that needs them.  On success *out owns device
+ * memory until stk_destroy.  Synchronous. */
 int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out);
 
 /* Release everything stk_setup allocated.  NULL is accepted. */
