@@ -56,14 +56,17 @@ enum { STK_F64 = 0, STK_F32 = 1 };
 enum { STK_PREC_FP64 = 0, STK_PREC_MIXED = 1 };
 /* Local solver of the patch smoother (Sec. 3.2): conjugate gradients on the
  * pressure Schur complement with a fixed number of steps, or until a relative
- * tolerance is met. */
-enum { STK_CG_FIXED = 0, STK_CG_TOL = 1 };
+ * tolerance is met; or Direct (the paper's exact local solver, Sec. 3.2): the
+ * inverse of the Schur complement of every patch type of a level is built
+ * once in FP64 (on the level's first smoothing step, which is then
+ * synchronous and allocates) and applied as one dense product per patch. */
+enum { STK_CG_FIXED = 0, STK_CG_TOL = 1, STK_LOCAL_DIRECT = 2 };
 
 typedef struct stk_options {
   int precision;         /* STK_PREC_FP64 or STK_PREC_MIXED (V-cycle in FP32, Sec. 4.3) */
   int gmres_restart;     /* restart length of the flexible GMRES, default 20           */
   int max_iter;          /* total GMRES iteration limit, default 200                    */
-  int local_cg_mode;     /* STK_CG_FIXED (default) or STK_CG_TOL                       */
+  int local_cg_mode;     /* STK_CG_FIXED (default), STK_CG_TOL or STK_LOCAL_DIRECT     */
   int local_cg_iters;    /* CG steps in FIXED mode, step limit in TOL mode; default 15 */
   double local_cg_tol;   /* relative CG residual in TOL mode, default 1e-8; FP32 smoothing
                           * uses max(local_cg_tol, 1e-6), the accuracy an FP32 CG reaches */
@@ -239,7 +242,9 @@ int stk_rhs(stk_problem* P, const int* psi_freq, const double* psi_amp, const in
  * first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
  * share the array: calls that overlap on the GPU race and must be ordered by
- * the caller.  Nothing in the array needs clearing between calls. */
+ * the caller.  Nothing in the array needs clearing between calls.  With the
+ * Direct local solver the level's inverses must exist already (built by a
+ * stk_smooth call on it), else STK_ESTATE. */
 int stk_smooth_static(stk_problem* P, int level, int dtype, void* x, const void* b);
 
 #ifdef __cplusplus

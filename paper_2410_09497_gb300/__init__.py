@@ -18,7 +18,7 @@ _LIBNAME = "libstokesmg.so"
 
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
-CG_FIXED, CG_TOL = 0, 1
+CG_FIXED, CG_TOL, LOCAL_DIRECT = 0, 1, 2
 _STATUS = {0: "STK_OK", -1: "STK_EINVAL", -2: "STK_ECUDA", -3: "STK_ENOMEM", -4: "STK_ENOCONV", -5: "STK_ETIMEOUT", -6: "STK_ESTATE"}
 
 

@@ -46,6 +46,13 @@ void free_level(stk::Level& L) {
   L.tab32 = nullptr;
   L.ptab64 = nullptr;
   L.ptab32 = nullptr;
+  for (void* p : {(void*)L.dirM64, (void*)L.dirM32, (void*)L.dirtab64, (void*)L.dirtab32})
+    if (p) cudaFree(p);
+  L.dirM64 = nullptr;
+  L.dirM32 = nullptr;
+  L.dirtab64 = nullptr;
+  L.dirtab32 = nullptr;
+  L.dir_ready = false;
 }
 
 void free_problem(stk_problem* P) {
@@ -136,7 +143,8 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
   }
   if (P->opt.gmres_restart < 1 || P->opt.gmres_restart > 60 || P->opt.max_iter < 1 || P->opt.local_cg_iters < 0 ||
       (P->opt.precision != STK_PREC_FP64 && P->opt.precision != STK_PREC_MIXED) ||
-      (P->opt.local_cg_mode != STK_CG_FIXED && P->opt.local_cg_mode != STK_CG_TOL)) {
+      (P->opt.local_cg_mode != STK_CG_FIXED && P->opt.local_cg_mode != STK_CG_TOL &&
+       P->opt.local_cg_mode != STK_LOCAL_DIRECT)) {
     delete P;
     return fail(nullptr, STK_EINVAL, "invalid options (restart in 1..60, max_iter >= 1, known modes)");
   }

@@ -343,6 +343,17 @@ cudaError_t fill_factors(stk_problem* P, Coarse3Factors& F, unsigned char* flag)
 
 }  // namespace
 
+cudaError_t invert_shifted(double* M, int64_t n, int64_t ld, cudaStream_t s) {
+  double* alpha = nullptr;
+  cudaError_t e = dev_alloc_async(&alpha, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  schur_shift<<<1, 256, 0, s>>>(M, n, ld, alpha);
+  add_shift<<<(unsigned)std::min<int64_t>((n * n + 255) / 256, 4096), 256, 0, s>>>(M, n, ld, alpha);
+  e = gauss_jordan(M, n, ld, 1, s);
+  const cudaError_t e2 = cudaFreeAsync(alpha, s);
+  return e != cudaSuccess ? e : e2;
+}
+
 cudaError_t acquire_coarse3(stk_problem* P) {
   if (P->coarse3f) return cudaSuccess;
   int dev = 0;

@@ -143,6 +143,14 @@ struct Level {
   PatchTables<double>* ptab64 = nullptr;  // device
   PatchTables<float>* ptab32 = nullptr;   // device
   bool eo_interior = false;  // continuous and interior 1D eigenbases both in even-odd order
+  // Direct local solver (built on first use): (S + a 1 1^T)^{-1} of every patch
+  // type of the level, column-major (2k+2)^3 squared, FP64 and FP32 copies, and
+  // device tables of 64 pointers indexed by t0 + 4 t1 + 16 t2 (NULL: absent)
+  bool dir_ready = false;
+  double* dirM64 = nullptr;
+  float* dirM32 = nullptr;
+  const double** dirtab64 = nullptr;
+  const float** dirtab32 = nullptr;
 };
 
 struct MgWork {
@@ -200,6 +208,12 @@ cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int 
 cudaError_t launch_patch_colour_cg(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x,
                                    int cg_tol_mode, int cg_iters, double cg_tol);
 cudaError_t launch_coarse_columns(const stk_problem* P, double* cols, int max_iter, double tol);
+// the local inverses of the Direct solver of a level (smoother.cu); synchronous
+cudaError_t ensure_direct(stk_problem* P, int level);
+// coarse3.cu: M <- (M + a 1 1^T)^{-1}, a = trace(M) / n^2, for a symmetric
+// positive semidefinite M (n x n, row stride ld) whose null space is the
+// constants; by Gauss-Jordan elimination on the stream
+cudaError_t invert_shifted(double* M, int64_t n, int64_t ld, cudaStream_t s);
 // one colour of `count` problems of the same degree (levels[i] of problem i),
 // kMaxPatchJobs problems per launch, on `stream`; local-solver options of Ps[0]
 cudaError_t launch_patch_colour_multi(const stk_problem* const* Ps, const int* levels, int count, int dtype,

@@ -79,7 +79,9 @@ struct PatchArgs {
   int cnt[3];     // patches of the colour per direction
   int part;       // mode 0: 0 every patch, 1 interior patches only, 2 boundary patches only
   int tlo[3], cint[3];  // the interior patches: t in [tlo, tlo + cint) per direction
-  int mode;       // 0: smoother colour, 1: coarse pseudo-inverse columns
+  int mode;       // 0: smoother colour, 1: coarse pseudo-inverse columns, 2: Schur complement columns
+  const T* const* dir;  // mode 0: (S + a 1 1^T)^{-1} per patch type t0 + 4 t1 + 16 t2 (NULL: CG)
+  int btype[3];   // mode 2: the patch type in each direction
   int cg_iters;   // FIXED: exact count; TOL: limit
   int cg_tol_mode;
   T cg_tol;
@@ -559,9 +561,39 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
     v[0] = v[1] = v[2] = 1;
   }
   PatchGeo g;
-  for (int d = 0; d < 3; ++d) g.type[d] = (v[d] == 1 ? 1 : 0) | (v[d] == A.n - 1 ? 2 : 0);
+  for (int d = 0; d < 3; ++d) g.type[d] = A.mode == 2 ? A.btype[d] : (v[d] == 1 ? 1 : 0) | (v[d] == A.n - 1 ? 2 : 0);
   // the boundary launch skips the interior patches (another launch took them)
   if (A.mode == 0 && A.part == 2 && g.type[0] == 0 && g.type[1] == 0 && g.type[2] == 0) return;
+
+  // SDc = S d per component for the pressure box Dd: (B S) Lam^{-1} (B S)^T d,
+  // passes x, y, z then z, y, x; returns the three component boxes to sum
+  auto schur_apply = [&]() -> T* {
+    patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Dd, Ba, 0, true, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
+    if constexpr (kFuseZ<K>) {
+      patch_pass<K, T, BTBF, EPI_NONE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 0, false, nullptr, nullptr, tb, g);
+      return Ba;
+    } else {
+      patch_pass<K, T, BT, EPI_SCALE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 2, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
+      return Bb;
+    }
+  };
+
+  if (A.mode == 2) {  // column blk of the Schur complement of a patch of types btype
+    for (int q = tid; q < C::NP; q += C::NT) Dd[(q % NPD) + BX * (q / NPD)] = (q == blk) ? T(1) : T(0);
+    __syncthreads();
+    const T* SDc = schur_apply();
+    for (int q = tid; q < C::NP; q += C::NT) {
+      const int o = (q % NPD) + BX * (q / NPD);
+      A.cols[(int64_t)blk * C::NP + q] = (double)(SDc[o] + SDc[BOX + o] + SDc[2 * BOX + o]);
+    }
+    return;
+  }
 
   // ---- gather F (velocity boxes in Ba) and G (pressure box in Pp = Ba + 8 BOX);
   // the padded plane (node 2k+1 of the continuous direction) of each velocity
@@ -623,26 +655,33 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   T rr = block_sum<T, C::NW>(s2, red_b);
   const T rr0 = rr;
 
-  // ---- conjugate gradients on the mean-free pressures
-  for (int it = 0; it < A.cg_iters; ++it) {
+  // ---- the local Schur system S P = R on mean-free pressures: Direct (a
+  // precomputed (S + a 1 1^T)^{-1} of this patch type, which maps a mean-free
+  // R to the mean-free solution) or conjugate gradients
+  const T* Mdir = (A.mode == 0 && A.dir) ? A.dir[g.type[0] + 4 * g.type[1] + 16 * g.type[2]] : nullptr;
+  if (Mdir) {
+    constexpr int NO = (C::NP + C::NT - 1) / C::NT;  // outputs per thread
+    T acc[NO];
+#pragma unroll
+    for (int u = 0; u < NO; ++u) acc[u] = T(0);
+    for (int j = 0; j < C::NP; ++j) {
+      const T rj = R[(j % NPD) + BX * (j / NPD)];
+      const T* col = Mdir + (int64_t)j * C::NP;  // column j, read across the threads
+#pragma unroll
+      for (int u = 0; u < NO; ++u)
+        if (tid + u * C::NT < C::NP) acc[u] = fma(col[tid + u * C::NT], rj, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+      const int q = tid + u * C::NT;
+      if (q < C::NP) Pp[(q % NPD) + BX * (q / NPD)] = acc[u];
+    }
+    __syncthreads();
+  }
+  for (int it = 0; !Mdir && it < A.cg_iters; ++it) {
     if (A.cg_tol_mode && rr <= A.cg_tol * A.cg_tol * rr0) break;
     if (!(rr > T(0))) break;
-    // SDc = S d per component: (B S) Lam^{-1} (B S)^T d, passes x, y, z then z, y, x
-    patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Dd, Ba, 0, true, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
-    T* SDc;
-    if constexpr (kFuseZ<K>) {
-      patch_pass<K, T, BTBF, EPI_NONE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 0, false, nullptr, nullptr, tb, g);
-      SDc = Ba;
-    } else {
-      patch_pass<K, T, BT, EPI_SCALE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 2, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
-      SDc = Bb;
-    }
+    T* SDc = schur_apply();
     T part = T(0);
     for (int q = tid; q < C::NP; q += C::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
@@ -845,7 +884,8 @@ static void fill_common(const stk_problem* P, const Level& L, PatchArgs<T>& a) {
   a.cg_tol = local_tol<T>(P->opt.local_cg_tol);
   a.cols = nullptr;
   a.part = 0;
-  for (int d = 0; d < 3; ++d) a.tlo[d] = a.cint[d] = 0;
+  a.dir = nullptr;
+  for (int d = 0; d < 3; ++d) a.tlo[d] = a.cint[d] = a.btype[d] = 0;
 }
 
 constexpr int kSplitInterior = 8192;  // interior patches per colour from which they get their own launch
@@ -885,6 +925,12 @@ static cudaError_t patch_colour(const stk_problem* P, const Level& L, const Patc
   a.cg_tol_mode = cg_tol_mode;
   a.cg_iters = cg_iters;
   a.cg_tol = local_tol<T>(cg_tol);
+  if (P->opt.local_cg_mode == STK_LOCAL_DIRECT && L.dir_ready) {
+    if constexpr (sizeof(T) == 8)
+      a.dir = L.dirtab64;
+    else
+      a.dir = L.dirtab32;
+  }
   interior_box(L.n, colour, cnt, a.tlo, a.cint);
   const int ni = a.cint[0] * a.cint[1] * a.cint[2];
   // Interior patches in their own launch (no dense transforms compiled in),
@@ -952,6 +998,76 @@ cudaError_t launch_patch_colour_multi(const stk_problem* const* Ps, const int* l
                                       int colour, void* const* r, void* const* x, cudaStream_t stream) {
   if (dtype == STK_F64) return patch_colour_multi<double>(Ps, levels, count, colour, r, x, stream);
   return patch_colour_multi<float>(Ps, levels, count, colour, r, x, stream);
+}
+
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// The Direct local solver of a level: for every patch type (t0, t1, t2) that
+// occurs, the columns S e_q of its Schur complement (patch kernel, mode 2,
+// FP64), then (S + a 1 1^T)^{-1} in place, plus an FP32 copy.  Built once,
+// synchronously; a failure leaves nothing allocated.
+cudaError_t ensure_direct(stk_problem* P, int level) {
+  Level& L = P->levels[level];
+  if (L.dir_ready) return cudaSuccess;
+  const int npd = 2 * P->k + 2;
+  const int64_t np = (int64_t)npd * npd * npd, nn = np * np;
+  bool present[4] = {false, false, false, false};
+  for (int v = 1; v <= L.n - 1; ++v) present[(v == 1 ? 1 : 0) | (v == L.n - 1 ? 2 : 0)] = true;
+  std::vector<int> combos;
+  for (int t2 = 0; t2 < 4; ++t2)
+    for (int t1 = 0; t1 < 4; ++t1)
+      for (int t0 = 0; t0 < 4; ++t0)
+        if (present[t0] && present[t1] && present[t2]) combos.push_back(t0 + 4 * t1 + 16 * t2);
+  const int nc = (int)combos.size();
+  cudaError_t e = dev_alloc(&L.dirM64, sizeof(double) * nn * nc);
+  if (e == cudaSuccess) e = dev_alloc(&L.dirM32, sizeof(float) * nn * nc);
+  if (e == cudaSuccess) e = dev_alloc(&L.dirtab64, sizeof(double*) * 64);
+  if (e == cudaSuccess) e = dev_alloc(&L.dirtab32, sizeof(float*) * 64);
+  std::vector<const double*> t64(64, nullptr);
+  std::vector<const float*> t32(64, nullptr);
+  for (int i = 0; e == cudaSuccess && i < nc; ++i) {
+    const int c = combos[i];
+    double* S = L.dirM64 + nn * i;
+    PatchArgs<double> a;
+    fill_common(P, L, a);
+    a.r = nullptr;
+    a.x = nullptr;
+    a.cols = S;
+    a.tab = L.ptab64;
+    a.colour = 0;
+    a.cnt[0] = a.cnt[1] = a.cnt[2] = 1;
+    a.mode = 2;
+    a.btype[0] = c % 4;
+    a.btype[1] = (c / 4) % 4;
+    a.btype[2] = c / 16;
+    e = dispatch_patch<double>(P->k, a, (int)np, P->stream);
+    if (e == cudaSuccess) e = invert_shifted(S, np, np, P->stream);
+    if (e == cudaSuccess) {
+      to_float_kernel<<<(unsigned)std::min<int64_t>((nn + 255) / 256, 4096), 256, 0, P->stream>>>(
+          S, L.dirM32 + nn * i, nn);
+      e = cudaGetLastError();
+    }
+    t64[c] = S;
+    t32[c] = L.dirM32 + nn * i;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(L.dirtab64, t64.data(), sizeof(double*) * 64, cudaMemcpyHostToDevice, P->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(L.dirtab32, t32.data(), sizeof(float*) * 64, cudaMemcpyHostToDevice, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(P->stream);
+    for (void* p : {(void*)L.dirM64, (void*)L.dirM32, (void*)L.dirtab64, (void*)L.dirtab32})
+      if (p) cudaFree(p);
+    L.dirM64 = nullptr;
+    L.dirM32 = nullptr;
+    L.dirtab64 = nullptr;
+    L.dirtab32 = nullptr;
+    return e;
+  }
+  L.dir_ready = true;
+  return cudaSuccess;
 }
 
 int patch_local_size(int k) {

@@ -207,6 +207,7 @@ cudaError_t ensure_coarse(stk_problem* P) {
 // ---------------------------------------------------------------- smoother
 cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void* b) {
   cudaError_t e = ensure_mg_workspace(P, dtype);
+  if (e == cudaSuccess && P->opt.local_cg_mode == STK_LOCAL_DIRECT) e = ensure_direct(P, level);
   if (e != cudaSuccess) return e;
   void* r = P->mg[dtype].r[level];
   for (int colour = 0; colour < 8; ++colour) {
@@ -224,6 +225,18 @@ cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void
 cudaError_t run_smooth_batch(stk_problem* const* Ps, const int* levels, int count, int dtype, void* const* x,
                              const void* const* b) {
   const cudaStream_t s = Ps[0]->stream;
+  if (Ps[0]->opt.local_cg_mode == STK_LOCAL_DIRECT) {
+    // the Direct local inverses belong to each problem's level: one launch per problem
+    for (int i = 0; i < count; ++i) {
+      stk_problem* P = Ps[i];
+      const cudaStream_t own = P->stream;
+      P->stream = s;
+      const cudaError_t e = run_smooth(P, levels[i], dtype, x[i], b[i]);
+      P->stream = own;
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   std::vector<void*> r(count);
   for (int i = 0; i < count; ++i) {
     cudaError_t e = ensure_mg_workspace(Ps[i], dtype);

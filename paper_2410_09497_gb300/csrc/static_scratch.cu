@@ -80,6 +80,11 @@ extern "C" int stk_smooth_static(stk_problem* P, int level, int dtype, void* x, 
              " bytes of residual scratch, the static array holds " + std::to_string(stk::kStaticScratchBytes);
     return STK_EINVAL;
   }
+  if (P->opt.local_cg_mode == STK_LOCAL_DIRECT && !P->levels[level].dir_ready) {
+    // building the Direct local inverses allocates: a stk_smooth call on the level does it
+    P->err = "smooth_static: the Direct local inverses of this level are not built yet";
+    return STK_ESTATE;
+  }
   void* r = nullptr;
   cudaError_t e = stk::scratch_address(&r);
   for (int colour = 0; e == cudaSuccess && colour < 8; ++colour) {
