@@ -13,7 +13,8 @@ The same JSON line carries sub-benchmarks of the other workloads:
 `apply_f32` (the FP32 apply of the V-cycle, same mesh), `sweep` (FP64 apply,
 64^3 cells, k = 1..5), `smooth` (one smoothing step, 64^3,
 k = 3, FP32 and FP64), `solve` (manufactured problem on 96^3 cells, k = 3,
-to 1e-8: mixed precision against plain FP64) and `batch` (64 uneven
+to 1e-8: mixed precision against plain FP64, with the Schur-CG and with the
+Direct local solver) and `batch` (64 uneven
 problems solved together against one after another); each can be resized or
 skipped with its flag (0 skips).
 
@@ -227,16 +228,18 @@ def run_solve_pair(args, stream, ws):
     """Mixed-precision and FP64 multigrid solves of the seeded manufactured problem to 1e-8."""
     import torch
 
-    from paper_2410_09497_gb300 import PREC_FP64, PREC_MIXED, StokesMG
+    from paper_2410_09497_gb300 import CG_FIXED, LOCAL_DIRECT, PREC_FP64, PREC_MIXED, StokesMG
     from seeded_inputs import manufactured_coefficients
 
     n, k = args.solve_n, args.solve_k
     out = {"workload": f"manufactured Stokes solve, RT_{k} x DGQ_{k}, {n}^3 cells, FGMRES(20) + V-cycle to 1e-8",
            "unit": "s/MDoF", "higher_is_better": False}
     coef = manufactured_coefficients(3000)
-    for name, prec in (("mixed", PREC_MIXED), ("fp64", PREC_FP64)):
+    runs = (("mixed", PREC_MIXED, CG_FIXED), ("fp64", PREC_FP64, CG_FIXED),
+            ("mixed_direct", PREC_MIXED, LOCAL_DIRECT), ("fp64_direct", PREC_FP64, LOCAL_DIRECT))
+    for name, prec, local in runs:
         with torch.cuda.stream(stream):
-            P = StokesMG(n, k, 1.0, precision=prec, stream=stream)
+            P = StokesMG(n, k, 1.0, precision=prec, stream=stream, local_cg_mode=local)
             N = P.layout()["n_total"]
             b = torch.empty(N, dtype=torch.float64, device="cuda")
             x = torch.zeros_like(b)
@@ -252,6 +255,9 @@ def run_solve_pair(args, stream, ws):
         out[name] = {"seconds": t, "s_per_MDoF": t / (N / 1e6), "dofs": N, "iterations": info["iterations"],
                      "nu": info["nu"], "relres": info["relres"], "converged": info["converged"]}
     out["mixed_speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["mixed_speedup_direct"] = out["fp64_direct"]["seconds"] / out["mixed_direct"]["seconds"]
+    out["local_solvers"] = ("mixed / fp64: Schur-complement CG, 15 steps (the paper's method); "
+                            "*_direct: the exact local solver (precomputed Schur-complement inverses)")
     out["value"] = out["mixed"]["s_per_MDoF"]
     # iterations as levels are added (the V-cycle's contraction does not depend
     # on h): the same manufactured problem on 4^3 .. 64^3 cells, mixed precision
