@@ -164,17 +164,23 @@ class Hierarchy:
     # ---------------------------------------------------------------- smoother
     def smooth(self, l: int, x: np.ndarray, b: np.ndarray) -> np.ndarray:
         """One step of Algorithm 2 on level l (colours 0..7, ascending)."""
+        x = x.copy()
+        for colour in range(8):
+            self.smooth_colour(l, colour, x, b)
+        return x
+
+    def smooth_colour(self, l: int, colour: int, x: np.ndarray, b: np.ndarray) -> np.ndarray:
+        """One colour of Algorithm 2 on level l, in place: the residual of the
+        current x, then every patch of the colour adds its local solve into x."""
         lev = self.levels[l]
         disc, A = lev.disc, lev.A
-        x = x.copy()
         npress = (2 * disc.k + 2) ** 3
-        for colour in range(8):
-            r = b - A @ x
-            r[~lev.free] = 0.0
-            for v in colour_vertices(disc.n, colour):
-                J = patch_dofs(disc, v)
-                Aj = A[J][:, J].toarray()
-                x[J] += self.local(Aj, npress, r[J])
+        r = b - A @ x
+        r[~lev.free] = 0.0
+        for v in colour_vertices(disc.n, colour):
+            J = patch_dofs(disc, v)
+            Aj = A[J][:, J].toarray()
+            x[J] += self.local(Aj, npress, r[J])
         return x
 
     # ------------------------------------------------------------ coarse solve

@@ -256,6 +256,25 @@ def test_prolongation_is_the_embedding(k):
     assert np.abs(uu - uu2).max() < 1e-13
 
 
+@pytest.mark.parametrize("n,k,nu,pf", [(2, 1, 1.0, 1.0), (2, 2, 0.7, 1.3), (3, 2, 1.0, 1.0), (2, 3, 1.0, 1.0)])
+def test_galerkin_product_is_the_coarse_matrix_with_doubled_penalty(n, k, nu, pf):
+    """The spaces are nested (Sec. 3), so for coarse functions the fine form
+    differs from the coarse one only through the penalty gamma_e ~ 1/h, twice
+    as large on the fine mesh; jumps across fine faces inside a coarse cell
+    vanish.  Hence P^T A_fine P is the coarse matrix assembled with twice the
+    penalty factor, and its divergence blocks are the coarse ones."""
+    C, F = Discretization(n, k, nu, pf), Discretization(2 * n, k, nu, pf)
+    P = prolongation(C, F)
+    G = (P.T @ F.assemble() @ P).tocsr()
+    A2 = Discretization(n, k, nu, 2 * pf).assemble()
+    assert abs(G - A2).max() <= 1e-13 * abs(A2).max()
+    A1 = C.assemble()
+    p0 = C.offsets[3]
+    assert abs(G[p0:] - A1[p0:]).max() <= 1e-13 * abs(A1).max()
+    # the velocity block does depend on the penalty: the identity is not vacuous
+    assert abs(G - A1).max() > 0.1 * abs(A1).max()
+
+
 # ---------------------------------------------------------- local solvers
 def test_direct_local_solver_is_exact_on_one_patch():
     """On the 2^3 mesh the single vertex patch holds every free DoF: one
@@ -265,6 +284,50 @@ def test_direct_local_solver_is_exact_on_one_patch():
     b = rhs(d, Manufactured(manufactured_coefficients(2)))
     x = H.smooth(0, np.zeros(d.N), b)
     assert np.linalg.norm(H.levels[0].A @ x - b) < 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_each_colour_leaves_its_patch_in_equilibrium(k):
+    """On the 3^3 mesh every colour holds one vertex patch.  After a colour's
+    update (Algorithm 2, exact local solver) the residual on that patch's DoFs
+    is zero in the velocity and a constant in the pressure (the local kernel).
+    After a whole step only the last colour's patch is in equilibrium, which
+    pins the ascending colour order."""
+    H = Hierarchy(3, k)
+    d = H.levels[0].disc
+    A = H.levels[0].A
+    npress = (2 * k + 2) ** 3
+    b = random_vector(19, d.N) * d.free_mask()
+    x0 = random_vector(20, d.N) * d.free_mask()
+
+    def imbalance(x, colour):
+        (v,) = colour_vertices(3, colour)
+        res = (b - A @ x)[patch_dofs(d, v)]
+        return max(np.abs(res[:-npress]).max(), np.ptp(res[-npress:])) / np.abs(b).max()
+
+    x = x0.copy()
+    for colour in range(8):
+        H.smooth_colour(0, colour, x, b)
+        assert imbalance(x, colour) < 1e-12
+    assert np.array_equal(x, H.smooth(0, x0, b))
+    assert imbalance(x, 7) < 1e-12 and imbalance(x, 0) > 1e-3
+
+
+def test_coarse_solve_is_exact():
+    """Sec. 3: the coarsest level (2^3 or 3^3 cells) is solved exactly: for a
+    consistent b = A x the solve returns x up to a constant pressure, and the
+    bordered system fixes that constant to a zero coefficient sum."""
+    for n, k in [(2, 1), (2, 3), (3, 1), (3, 2)]:
+        H = Hierarchy(n, k)
+        d = H.levels[0].disc
+        A = H.levels[0].A
+        xt = random_vector(21, d.N) * d.free_mask()
+        x = H.coarse_solve(A @ xt)
+        p0 = d.offsets[3]
+        assert np.abs(x[:p0] - xt[:p0]).max() < 1e-10 * np.abs(xt).max()
+        dp = x[p0:] - xt[p0:]
+        assert np.ptp(dp) < 1e-10 * np.abs(xt).max()
+        assert abs(x[p0:].sum()) < 1e-10 * np.abs(xt).max() * len(dp)
 
 
 @pytest.mark.parametrize("n,k", [(3, 1), (4, 2), (3, 3)])
@@ -315,6 +378,41 @@ def test_three_steps_for_k3():
     _, info = H.solve(rhs(d, Manufactured(manufactured_coefficients(0))), tol=1e-8)
     assert info["iterations"] <= GOLDEN["max_gmres_steps_k_ge_3"]["value"]
     assert info["nu"] <= 3.0
+
+
+@pytest.mark.parametrize("restart", [20, 2])
+def test_fgmres_minimises_the_residual(restart):
+    """The V-cycle from x0 = 0 is a fixed linear map M, so flexible GMRES is
+    right-preconditioned GMRES: within a restart cycle from residual r its
+    j-th residual is min_c ||r - [A M w_0, ..., A M w_{j-1}] c|| over the
+    Krylov vectors w_0 = r, w_{i+1} = A M w_i.  Brute force by least squares
+    on those vectors, restart by restart."""
+    H = Hierarchy(4, 1)
+    d = H.levels[-1].disc
+    A = H.levels[-1].A
+    b = A @ (random_vector(23, d.N) * d.free_mask())
+    steps = 4
+    _, info = H.solve(b, tol=1e-30, restart=restart, maxit=steps)
+    bnorm = np.linalg.norm(b)
+    x = np.zeros(d.N)
+    hist = [1.0]
+    while len(hist) <= steps:
+        r = b - A @ x
+        W, Z = [r / np.linalg.norm(r)], []
+        for _ in range(min(restart, steps + 1 - len(hist))):
+            Z.append(H.vcycle(W[-1]))
+            w = A @ Z[-1]
+            W.append(w / np.linalg.norm(w))
+            K = np.stack(W[1:], 1)
+            c = np.linalg.lstsq(K, r, rcond=None)[0]
+            hist.append(np.linalg.norm(r - K @ c) / bnorm)
+        for zi, ci, wn in zip(Z, c, [np.linalg.norm(A @ z) for z in Z]):
+            x = x + (ci / wn) * zi
+    got = np.array(info["residuals"])
+    ref = np.array(hist)
+    assert len(got) == steps + 1
+    assert np.all(np.abs(got - ref) <= 1e-10 + 1e-6 * ref), (got, ref)
+    assert ref[-1] < 1e-3  # the V-cycle preconditioner is doing its job
 
 
 def test_fractional_iteration_count_definition():
