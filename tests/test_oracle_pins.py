@@ -313,6 +313,48 @@ def test_each_colour_leaves_its_patch_in_equilibrium(k):
     assert imbalance(x, 7) < 1e-12 and imbalance(x, 0) > 1e-3
 
 
+@pytest.mark.parametrize("k", [1, 2])
+def test_schur_cg_minimises_the_energy_error(k):
+    """Sec. 3.2: the pressure after j CG steps on S P = g (S = B A^-1 B^T,
+    g = B A^-1 F - G made mean-free) is the S-energy-best approximation of
+    the exact P in the Krylov space span{g, S g, ..., S^(j-1) g}; the velocity
+    is then A^-1 (F - B^T P).  Brute force by the Galerkin condition on an
+    orthonormal basis of the explicit Krylov vectors."""
+    n = 3
+    d = Discretization(n, k)
+    A = d.assemble()
+    (v,) = colour_vertices(n, 5)
+    J = patch_dofs(d, v)
+    Aj = A[J][:, J].toarray()
+    npress = (2 * k + 2) ** 3
+    nv = len(J) - npress
+    r = random_vector(29, d.N)[J]
+    F, G = r[:nv], r[nv:]
+    Av = Aj[:nv, :nv]
+    B = Aj[nv:, :nv]
+    S = B @ np.linalg.solve(Av, B.T)
+    g = B @ np.linalg.solve(Av, F) - G
+    g = g - g.mean()
+    Pstar = np.linalg.lstsq(S, g, rcond=None)[0]
+    Pstar = Pstar - Pstar.mean()
+    Ainv = lambda w: np.linalg.solve(Av, w)
+    for j in range(1, 6):
+        K = [g]
+        for _ in range(j - 1):
+            K.append(S @ K[-1])
+        Q = np.linalg.qr(np.stack(K, 1))[0]
+        Pj = Q @ np.linalg.solve(Q.T @ S @ Q, Q.T @ g)
+        out = schur_cg(Ainv, B, F, G, "schur", j)
+        assert np.abs(out[nv:] - Pj).max() <= 1e-9 * np.abs(Pj).max(), j
+        assert np.abs(out[:nv] - Ainv(F - B.T @ Pj)).max() <= 1e-9 * np.abs(out[:nv]).max()
+        # the energy error decreases strictly along the iteration
+        e = Pj - Pstar
+        err = e @ S @ e
+        if j > 1:
+            assert err < prev
+        prev = err
+
+
 def test_coarse_solve_is_exact():
     """Sec. 3: the coarsest level (2^3 or 3^3 cells) is solved exactly: for a
     consistent b = A x the solve returns x up to a constant pressure, and the
