@@ -114,6 +114,31 @@ int stk_num_levels(const stk_problem* P, int* nlevels);
 int stk_layout(const stk_problem* P, int level, int* n_cells, int64_t* n_vel_component,
                int64_t* n_pressure, int64_t* n_total);
 
+/* The 1D fast-diagonalization data of the vertex-patch local solver (Sec. 3.2,
+ * eq. `inverse2d` and eq. `fast_inverse`) exactly as stk_setup builds it for a
+ * level of n cells per side, degree k, viscosity nu and penalty factor:
+ * the generalized eigenpairs K S = M S diag(lambda), S^T M S = I, of one 1D
+ * patch operator (K and M of the two cells of a patch; K without the factor nu).
+ *   direction 0     the continuous direction of a velocity component: the
+ *                   2k+1 patch-interior nodes, K the 1D stiffness, M the 1D
+ *                   mass of the continuous basis;
+ *   direction 1..4  a discontinuous direction of boundary type direction - 1
+ *                   (0 interior patch, 1 patch on the lower mesh boundary,
+ *                   2 on the upper one, 3 both): the 2k+2 nodes, K the 1D
+ *                   interior-penalty operator with this level's penalty, M
+ *                   the diagonal Gauss mass.
+ * S (row-major dim x dim, eigenvectors in its columns) and lambda (dim) are
+ * host arrays of the caller with room for (2k+2)^2 and 2k+2 doubles; *dim
+ * receives 2k+1 or 2k+2 and *even_odd 1 when the columns are ordered with the
+ * eigenvectors symmetric under the patch's reflection first and the
+ * antisymmetric ones after (the kernels then transform lines in even-odd
+ * form), else 0.  Host computation only: needs no GPU, touches no device and
+ * keeps no state.  STK_EINVAL (message in stk_last_error(NULL)) for k outside
+ * 1..5, n < 2, nu or penalty_factor not positive, direction outside 0..4 or a
+ * NULL pointer; STK_ENOMEM if a host allocation fails. */
+int stk_patch_eigen(int n, int k, double nu, double penalty_factor, int direction, double* S, double* lambda,
+                    int* dim, int* even_odd);
+
 /* y = A x on one level: the matrix-free Stokes operator of Algorithm 1 (cell,
  * interior-face and boundary-face loops of eq. `bilinear`, with the divergence
  * blocks of eq. `weak_form`), evaluated through its Kronecker form on the

@@ -11,7 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "solve_batch", "F64", "F32"]
+__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "patch_eigen", "solve_batch", "smooth_batch", "F64", "F32"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBNAME = "libstokesmg.so"
@@ -93,6 +93,7 @@ def load_library():
         "stk_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_smooth_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P)]),
+        "stk_patch_eigen": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -107,6 +108,25 @@ def layout_sizes(n: int, k: int):
     m = n * (k + 1)
     nv = (m + 1) * m * m
     return nv, m ** 3, 3 * nv + m ** 3
+
+
+def patch_eigen(n: int, k: int, direction: int, nu: float = 1.0, penalty_factor: float = 1.0):
+    """(S, lam, even_odd) of stk_patch_eigen: the 1D fast-diagonalization
+    eigenpairs the library builds for a level of n cells per side (host
+    computation, no GPU needed).  S is a dim x dim NumPy array with the
+    eigenvectors in its columns."""
+    import numpy as np
+
+    lib = load_library()
+    npd = 2 * k + 2
+    S = np.zeros(npd * npd)
+    lam = np.zeros(npd)
+    dim, eo = ctypes.c_int(), ctypes.c_int()
+    rc = lib.stk_patch_eigen(int(n), int(k), float(nu), float(penalty_factor), int(direction), S.ctypes.data, lam.ctypes.data, ctypes.byref(dim), ctypes.byref(eo))
+    if rc != 0:
+        raise StokesError(rc, (lib.stk_last_error(None) or b"").decode())
+    d = dim.value
+    return S[: d * d].reshape(d, d).copy(), lam[:d].copy(), bool(eo.value)
 
 
 class StokesMG:

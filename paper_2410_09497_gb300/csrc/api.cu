@@ -1,6 +1,7 @@
 // C ABI of libstokesmg: setup, teardown, layout queries and the operator
 // entry points.  Every function returns a status code and never throws.
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -109,6 +110,28 @@ int stk_default_options(stk_options* opt) {
   opt->penalty_factor = 1.0;
   opt->stream = nullptr;
   opt->use_graphs = 1;
+  return STK_OK;
+}
+
+int stk_patch_eigen(int n, int k, double nu, double penalty_factor, int direction, double* S, double* lambda,
+                    int* dim, int* even_odd) {
+  if (k < 1 || k > stk::kMaxDegree) return fail(nullptr, STK_EINVAL, "patch_eigen: degree k must be in 1..5");
+  if (n < 2) return fail(nullptr, STK_EINVAL, "patch_eigen: n must be at least 2");
+  if (!(nu > 0.0) || !(penalty_factor > 0.0))
+    return fail(nullptr, STK_EINVAL, "patch_eigen: viscosity and penalty factor must be positive");
+  if (direction < 0 || direction > 4) return fail(nullptr, STK_EINVAL, "patch_eigen: direction must be in 0..4");
+  if (!S || !lambda || !dim || !even_odd) return fail(nullptr, STK_EINVAL, "patch_eigen: NULL output pointer");
+  try {
+    const stk::PatchTables1D p = stk::build_patch_tables(stk::build_tables(k, 1.0 / n, nu, penalty_factor));
+    const std::vector<double>& vs = direction == 0 ? p.SC : p.SD[direction - 1];
+    const std::vector<double>& vl = direction == 0 ? p.LC : p.LD[direction - 1];
+    std::copy(vs.begin(), vs.end(), S);
+    std::copy(vl.begin(), vl.end(), lambda);
+    *dim = (int)vl.size();
+    *even_odd = (direction == 0 ? p.eo_c : p.eo_d[direction - 1]) ? 1 : 0;
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, STK_ENOMEM, "patch_eigen: host allocation failed");
+  }
   return STK_OK;
 }
 

@@ -1,0 +1,82 @@
+"""Host logic of the library, checked without a GPU: the 1D fast-diagonalization
+eigenpairs that stk_setup builds for the vertex-patch local solver (Sec. 3.2,
+eq. `inverse2d`, eq. `fast_inverse`), read through stk_patch_eigen.
+
+The 1D patch operators are taken as principal submatrices of global 1D
+matrices assembled independently in tests/test_oracle_pins.py (its Kronecker
+check builds them by 1D Gauss quadrature); the library's tables must satisfy
+K S = M S diag(lambda), S^T M S = I, lambda > 0, and, where it reports the
+even-odd order, have reflection-symmetric columns first and antisymmetric ones
+after.
+"""
+import numpy as np
+import pytest
+
+from test_oracle_pins import _one_d
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2410_09497_gb300 import build
+
+    build.build()
+    import paper_2410_09497_gb300 as m
+
+    return m
+
+
+def _patch_operators(n, k, pf, direction):
+    """(K, M) of one 1D patch operator from the global 1D matrices (nu removed)."""
+    gamma = pf * (k + 1) * (k + 2) * n
+    LC, MC, _, LD, MD = _one_d(n, k, 1.0, gamma)
+    k1 = k + 1
+    if direction == 0:  # vertex 2 of a 4-cell line: the interior nodes of cells 1 and 2
+        idx = np.arange(k1 + 1, 3 * k1)
+        return LC[np.ix_(idx, idx)], MC[np.ix_(idx, idx)]
+    first = {1: 1, 2: 0, 3: n - 2, 4: 0}[direction]  # lower cell of the patch
+    idx = np.arange(first * k1, (first + 2) * k1)
+    return LD[np.ix_(idx, idx)], MD[np.ix_(idx, idx)]
+
+
+CASES = [(4, 0), (4, 1), (4, 2), (4, 3), (2, 4)]  # direction 4 (both boundaries) needs n = 2
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n,direction", CASES)
+def test_fdm_eigenpairs(binding, k, n, direction):
+    nu, pf = (2.5, 1.5) if k == 3 else (1.0, 1.0)
+    S, lam, eo = binding.patch_eigen(n, k, direction, nu=nu, penalty_factor=pf)
+    K, M = _patch_operators(n, k, pf, direction)
+    dim = 2 * k + 1 if direction == 0 else 2 * k + 2
+    assert S.shape == (dim, dim) and K.shape == (dim, dim)
+    scale = np.abs(K).max()
+    assert np.abs(K @ S - M @ S * lam).max() <= 1e-11 * scale * np.abs(S).max()
+    assert np.abs(S.T @ M @ S - np.eye(dim)).max() <= 1e-12
+    assert lam.min() > 0  # continuous stiffness with both end nodes removed / coercive SIPG
+    # the operators of direction 0, 1 (interior) and 4 (both boundaries) are
+    # symmetric under the reflection of the patch, those of 2 and 3 are not
+    assert eo == (direction in (0, 1, 4))
+    if eo:
+        R = S[::-1]
+        ne = (dim + 1) // 2
+        assert np.abs(R[:, :ne] - S[:, :ne]).max() <= 1e-10 * np.abs(S).max()
+        assert np.abs(R[:, ne:] + S[:, ne:]).max() <= 1e-10 * np.abs(S).max()
+
+
+def test_patch_eigen_rejects_invalid_arguments(binding):
+    lib = binding.load_library()
+    S = np.zeros(144)
+    lam = np.zeros(12)
+    import ctypes
+
+    d, e = ctypes.c_int(), ctypes.c_int()
+    args = lambda n, k, nu, pf, dirn: lib.stk_patch_eigen(n, k, nu, pf, dirn, S.ctypes.data, lam.ctypes.data, ctypes.byref(d), ctypes.byref(e))
+    assert args(4, 0, 1.0, 1.0, 0) == -1
+    assert args(4, 6, 1.0, 1.0, 0) == -1
+    assert args(1, 2, 1.0, 1.0, 0) == -1
+    assert args(4, 2, 0.0, 1.0, 0) == -1
+    assert args(4, 2, 1.0, -1.0, 0) == -1
+    assert args(4, 2, 1.0, 1.0, 5) == -1
+    assert b"direction" in lib.stk_last_error(None)
+    assert lib.stk_patch_eigen(4, 2, 1.0, 1.0, 0, None, lam.ctypes.data, ctypes.byref(d), ctypes.byref(e)) == -1
+    assert args(4, 2, 1.0, 1.0, 1) == 0 and d.value == 6
