@@ -457,6 +457,19 @@ def test_fgmres_minimises_the_residual(restart):
     assert ref[-1] < 1e-3  # the V-cycle preconditioner is doing its job
 
 
+@pytest.mark.parametrize("k,local", [(2, "lu"), (2, ("schur", 15)), (4, "lu")])
+def test_table2_three_steps_to_1e6(k, local):
+    """Table 2: three GMRES steps reach a relative residual of 1e-6 for RT_2
+    and RT_4 (quoted on 32^3 cells; the counts are flat under refinement,
+    Sec. 3.3, so the 4^3 mesh stands in), with the Direct (exact) and the
+    Schur-complement local solver."""
+    H = Hierarchy(4, k, local=local)
+    d = H.levels[-1].disc
+    _, info = H.solve(rhs(d, Manufactured(manufactured_coefficients(0))), tol=1e-6)
+    assert info["converged"]
+    assert info["iterations"] <= GOLDEN["table2_iterations_tol_1e-6"][str(k)]
+
+
 def test_fractional_iteration_count_definition():
     # reduction of exactly 1e-8 in n steps gives nu = n (Sec. 3.3, read with a division)
     n = 3
