@@ -17,6 +17,8 @@ Modules
   transfer      prolongation by interpolation (canonical embedding, Sec. 3).
   multigrid     coloured vertex-patch smoother (Algorithm 2), V-cycle,
                 coarse solve, flexible GMRES, Schur-complement local solver.
+  planar        the same method on the unit square (Kronecker-form operator,
+                2 x 2-cell patches in four colours) for the 2D counts of Table 1.
 
 Parity status of each function is stated in its docstring; functions without
 an independent pin say "parity unpinned".

@@ -51,6 +51,7 @@ class Discretization:
         self.ext = [tuple(m + 1 if d == c else m for d in range(3)) for c in range(3)] + [(m, m, m)]
         nv = (m + 1) * m * m
         self.offsets = [0, nv, 2 * nv, 3 * nv]
+        self.pressure_start = 3 * nv
         self.n_vel_component = nv
         self.n_pressure = m ** 3
         self.N = 3 * nv + m ** 3

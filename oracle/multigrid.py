@@ -148,6 +148,8 @@ class Level:
 class Hierarchy:
     """Mesh hierarchy n_L = n, n_{l-1} = n_l / 2, down to the coarsest mesh (2 or 3 cells per side)."""
 
+    n_colours = 8
+
     def __init__(self, n: int, k: int, nu: float = 1.0, penalty_factor: float = 1.0, local="lu"):
         sizes = [n]
         while sizes[-1] % 2 == 0 and sizes[-1] > 3:
@@ -155,17 +157,30 @@ class Hierarchy:
         if sizes[-1] not in (2, 3):
             raise ValueError("mesh size must be 2 or 3 times a power of two")
         sizes = sizes[::-1]
-        self.levels = [Level(Discretization(s, k, nu, penalty_factor)) for s in sizes]
+        self.levels = [Level(self._discretization(s, k, nu, penalty_factor)) for s in sizes]
         for l in range(1, len(self.levels)):
-            self.levels[l].P = prolongation(self.levels[l - 1].disc, self.levels[l].disc)
+            self.levels[l].P = self._prolongation(self.levels[l - 1].disc, self.levels[l].disc)
         self.local = LocalSolver(local)
         self._coarse = None
 
+    # the pieces that depend on the space dimension
+    def _discretization(self, n, k, nu, penalty_factor):
+        return Discretization(n, k, nu, penalty_factor)
+
+    def _prolongation(self, coarse, fine):
+        return prolongation(coarse, fine)
+
+    def _patches(self, disc, colour):
+        return [patch_dofs(disc, v) for v in colour_vertices(disc.n, colour)]
+
+    def _npress(self, disc):
+        return (2 * disc.k + 2) ** 3
+
     # ---------------------------------------------------------------- smoother
     def smooth(self, l: int, x: np.ndarray, b: np.ndarray) -> np.ndarray:
-        """One step of Algorithm 2 on level l (colours 0..7, ascending)."""
+        """One step of Algorithm 2 on level l (colours in ascending order)."""
         x = x.copy()
-        for colour in range(8):
+        for colour in range(self.n_colours):
             self.smooth_colour(l, colour, x, b)
         return x
 
@@ -174,11 +189,10 @@ class Hierarchy:
         current x, then every patch of the colour adds its local solve into x."""
         lev = self.levels[l]
         disc, A = lev.disc, lev.A
-        npress = (2 * disc.k + 2) ** 3
+        npress = self._npress(disc)
         r = b - A @ x
         r[~lev.free] = 0.0
-        for v in colour_vertices(disc.n, colour):
-            J = patch_dofs(disc, v)
+        for J in self._patches(disc, colour):
             Aj = A[J][:, J].toarray()
             x[J] += self.local(Aj, npress, r[J])
         return x
@@ -193,7 +207,7 @@ class Hierarchy:
             Af = lev.A[f][:, f].toarray()
             nf = Af.shape[0]
             e = np.zeros(disc.N)
-            e[disc.offsets[3]:] = 1.0
+            e[disc.pressure_start:] = 1.0
             e = e[f]
             K = np.zeros((nf + 1, nf + 1))
             K[:nf, :nf] = Af
@@ -291,6 +305,7 @@ def project_pressure_mean(disc: Discretization, x: np.ndarray) -> np.ndarray:
     """Shift the pressure so that its L2 mean is zero: sum_i W_i p_i = 0."""
     x = x.copy()
     W = disc.pressure_weights()
-    p = x[disc.offsets[3]:]
-    x[disc.offsets[3]:] = p - (W @ p) / W.sum()
+    p0 = disc.pressure_start
+    p = x[p0:]
+    x[p0:] = p - (W @ p) / W.sum()
     return x

@@ -194,6 +194,23 @@ def test_smooth_field_energy_and_divergence(n, k):
     assert abs(q @ (A @ u) - (-1.0 / 216.0)) < 1e-13
 
 
+@pytest.mark.parametrize("n,k,pf", [(2, 1, 1.0), (3, 2, 1.7)])
+def test_boundary_penalty_closed_form(n, k, pf):
+    """u = (b(x), 0, 0), b = s(1-s), has zero normal trace but tangential
+    trace b(x) on the four faces y, z in {0, 1}, where d_n u = 0; the Nitsche
+    terms of eq. `bilinear` add 2 gamma int b^2 = 2 gamma / 30 per face:
+    a_h(u, u) = 1/3 + 8 gamma / 30."""
+    d = Discretization(n, k, 1.0, pf)
+    E = d.ext[0]
+    g = np.arange(E[0] * E[1] * E[2])
+    i0 = g % E[0]
+    cell = np.minimum(i0 // (k + 1), n - 1)
+    x = (cell + d.zC[i0 - cell * (k + 1)]) * d.h
+    u = np.zeros(d.N)
+    u[g] = x * (1 - x)
+    assert abs(u @ (d.assemble() @ u) - (1.0 / 3.0 + 8.0 * d.gamma / 30.0)) < 1e-12 * d.gamma
+
+
 def test_apply_rows_matches_assembly():
     d = Discretization(3, 2)
     A = d.assemble()
