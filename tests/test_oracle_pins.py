@@ -211,6 +211,21 @@ def test_boundary_penalty_closed_form(n, k, pf):
     assert abs(u @ (d.assemble() @ u) - (1.0 / 3.0 + 8.0 * d.gamma / 30.0)) < 1e-12 * d.gamma
 
 
+def test_pressure_weights_integrate_polynomials():
+    """The weights of the zero-mean pressure projection are int psi_i: they
+    integrate every field of the pressure space exactly, e.g. x^a y^b z^c with
+    a, b, c <= k (integral 1 / ((a+1)(b+1)(c+1)))."""
+    for n, k in [(2, 1), (3, 2)]:
+        d = Discretization(n, k)
+        W = d.pressure_weights()
+        m = d.m
+        g = np.arange(m)
+        x = (g // (k + 1) + d.zD[g % (k + 1)]) * d.h
+        X = [np.kron(np.ones(m * m), x), np.kron(np.kron(np.ones(m), x), np.ones(m)), np.kron(x, np.ones(m * m))]
+        for a, b, c in [(0, 0, 0), (k, 0, 0), (0, k, 1), (1, 1, k)]:
+            assert abs(W @ (X[0] ** a * X[1] ** b * X[2] ** c) - 1.0 / ((a + 1) * (b + 1) * (c + 1))) < 1e-14
+
+
 def test_apply_rows_matches_assembly():
     d = Discretization(3, 2)
     A = d.assemble()
