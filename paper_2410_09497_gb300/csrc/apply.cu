@@ -392,12 +392,10 @@ static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, cons
   a.nchunks = (L.n + a.chunk - 1) / a.chunk;
   dim3 grid(tiles * a.nchunks, 3);
   const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
-  static bool attr_set = false;  // per instantiation; the attribute is per device function
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(apply_velocity_kernel<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  static std::atomic<unsigned long long> smem_set{0};
+  {
+    const cudaError_t e = allow_dynamic_smem(apply_velocity_kernel<K, T>, smem, smem_set);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   if (stages & 1) apply_velocity_kernel<K, T><<<grid, Cfg::NT, smem, s>>>(a);
   if (stages & 2) {

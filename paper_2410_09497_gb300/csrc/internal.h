@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <memory>
 #include <string>
 #include <vector>
@@ -27,6 +28,22 @@ cudaError_t dev_alloc_async(T** p, size_t bytes, cudaStream_t s) {
 template <typename T>
 cudaError_t host_alloc_pinned(T** p, size_t bytes) {
   return host_alloc_pinned(reinterpret_cast<void**>(p), bytes);
+}
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` (needed above
+// 48 KB) once per device: the attribute belongs to the function on the device
+// that is current, so `done` keeps one bit per device.  Two threads making the
+// first call together both set it, which is harmless.
+template <typename Kernel>
+cudaError_t allow_dynamic_smem(Kernel* fn, size_t bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
 }
 
 constexpr int kMaxDegree = 5;

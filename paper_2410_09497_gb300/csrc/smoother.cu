@@ -819,13 +819,11 @@ template <int K, typename T>
 static cudaError_t launch_patch_k(PatchArgs<T> a, int nblocks, cudaStream_t s) {
   using C = PatchCfg<K>;
   const size_t smem = patch_smem_bytes<K>(sizeof(T));
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(patch_kernel<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(patch_kernel_interior<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> smem_set{0}, smem_set_interior{0};
+  {
+    cudaError_t e = allow_dynamic_smem(patch_kernel<K, T>, smem, smem_set);
+    if (e == cudaSuccess) e = allow_dynamic_smem(patch_kernel_interior<K, T>, smem, smem_set_interior);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   if (nblocks > 0) {
     if (a.mode == 0 && a.part == 1)
@@ -851,12 +849,10 @@ template <int K, typename T>
 static cudaError_t launch_patch_multi_k(const PatchArgs<T>& a, const PatchJobs<T>& J, int nblocks, cudaStream_t s) {
   using C = PatchCfg<K>;
   const size_t smem = patch_smem_bytes<K>(sizeof(T));
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(patch_kernel_multi<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> smem_set{0};
+  {
+    const cudaError_t e = allow_dynamic_smem(patch_kernel_multi<K, T>, smem, smem_set);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   if (nblocks > 0) patch_kernel_multi<K, T><<<nblocks, C::NT, smem, s>>>(a, J);
   return cudaGetLastError();
@@ -1137,23 +1133,15 @@ cudaError_t launch_coarse_solve(const stk_problem* P, int dtype, const void* b, 
   const size_t smem = sizeof(double) * NL;
 #define STK_CS_CASE(KK)                                                                                       \
   case KK: {                                                                                                  \
-    static bool attr64 = false, attr32 = false;                                                               \
+    static std::atomic<unsigned long long> set64{0}, set32{0};                                               \
     if (dtype == STK_F64) {                                                                                   \
-      if (!attr64) {                                                                                          \
-        e = cudaFuncSetAttribute(coarse_solve_kernel<KK, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)smem);                                                                  \
-        if (e != cudaSuccess) return e;                                                                       \
-        attr64 = true;                                                                                        \
-      }                                                                                                       \
+      e = allow_dynamic_smem(coarse_solve_kernel<KK, double>, smem, set64);                                   \
+      if (e != cudaSuccess) return e;                                                                         \
       coarse_solve_kernel<KK, double><<<blocks, 256, smem, P->stream>>>(P->coarse_inv, (const double*)b,      \
                                                                           (double*)x, L.m);                  \
     } else {                                                                                                  \
-      if (!attr32) {                                                                                          \
-        e = cudaFuncSetAttribute(coarse_solve_kernel<KK, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                 (int)smem);                                                                  \
-        if (e != cudaSuccess) return e;                                                                       \
-        attr32 = true;                                                                                        \
-      }                                                                                                       \
+      e = allow_dynamic_smem(coarse_solve_kernel<KK, float>, smem, set32);                                    \
+      if (e != cudaSuccess) return e;                                                                         \
       coarse_solve_kernel<KK, float><<<blocks, 256, smem, P->stream>>>(P->coarse_inv, (const float*)b,        \
                                                                          (float*)x, L.m);                    \
     }                                                                                                         \
