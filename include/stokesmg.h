@@ -31,6 +31,12 @@
  *          done in that precision.
  *  Errors: 0 = STK_OK; negative codes below.  No call aborts, throws or
  *          exits; stk_last_error() gives a message for the last failure.
+ *  Threads: distinct problems may be used from different host threads at
+ *          once (the shared coarse factors and launch attributes are
+ *          synchronised), except that stk_smooth_static calls share one
+ *          scratch array; one problem must not be used by two threads at
+ *          once.  The messages read through stk_last_error(NULL) are kept
+ *          per thread.
  */
 #ifndef STOKESMG_H
 #define STOKESMG_H
