@@ -93,7 +93,9 @@ typedef struct stk_solve_info {
   double residuals[256];    /* relative residual after each iteration, [0] = 1          */
 } stk_solve_info;
 
-/* Fill *opt with the defaults listed above.  Returns STK_EINVAL if opt is NULL. */
+/* Fill *opt with the defaults listed above: the solver settings of Sec. 3.3
+ * (GMRES preconditioned by one V-cycle, about 15 local CG steps) where the
+ * paper states them.  Returns STK_EINVAL if opt is NULL. */
 int stk_default_options(stk_options* opt);
 
 /* Build the mesh hierarchy and the 1D tables of every level (Sec. 2.3,
@@ -105,18 +107,22 @@ int stk_default_options(stk_options* opt);
  * memory until stk_destroy.  Synchronous. */
 int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out);
 
-/* Release everything stk_setup allocated.  NULL is accepted. */
+/* Release everything stk_setup allocated (bookkeeping, no counterpart in the
+ * paper).  NULL is accepted. */
 int stk_destroy(stk_problem* P);
 
 /* Message of the last failed call on P (or of the last failed stk_setup when
- * P is NULL).  The string stays valid until the next call on P. */
+ * P is NULL); error reporting has no counterpart in the paper.  The string
+ * stays valid until the next call on P. */
 const char* stk_last_error(const stk_problem* P);
 
-/* Number of levels of the hierarchy. */
+/* Number of levels of the mesh hierarchy of the multigrid method (Sec. 3:
+ * nested meshes obtained by uniform refinement of the coarsest one). */
 int stk_num_levels(const stk_problem* P, int* nlevels);
 
 /* Cells per side, per-velocity-component length, pressure length and total
- * length N of the vectors of one level. */
+ * length N of the vectors of one level: the DoF counts of the RT_k x DGQ_k
+ * spaces (Sec. 2.1) in the layout described above. */
 int stk_layout(const stk_problem* P, int level, int* n_cells, int64_t* n_vel_component,
                int64_t* n_pressure, int64_t* n_total);
 
@@ -152,8 +158,8 @@ int stk_patch_eigen(int n, int k, double nu, double penalty_factor, int directio
  * pressure rows: (q, div u).  x and y must not alias. */
 int stk_apply(stk_problem* P, int level, int dtype, const void* x, void* y);
 
-/* One of the two kernels of stk_apply: stage 0 writes the velocity rows of
- * y = A x, stage 1 the pressure rows; the other rows of y are left untouched.
+/* One of the two kernels of stk_apply (Algorithm 1 split by test space): stage
+ * 0 writes the velocity rows of y = A x, stage 1 the pressure rows; the other rows of y are left untouched.
  * Calling stage 0 then stage 1 is exactly stk_apply.  Lets a caller time the
  * two kernels separately on the library's stream. */
 int stk_apply_stage(stk_problem* P, int level, int dtype, int stage, const void* x, void* y);
@@ -181,9 +187,9 @@ int stk_restrict(stk_problem* P, int fine_level, int dtype, const void* rf, void
  * allocates that dtype's multigrid workspace (three vectors per level). */
 int stk_smooth(stk_problem* P, int level, int dtype, void* x, const void* b);
 
-/* One smoothing step (as stk_smooth) of `count` problems of the same degree
- * k, batched (the patch launches are not in the paper, which smooths one
- * problem): per colour, every problem's colour residual, then ONE launch of
+/* One smoothing step (as stk_smooth: Algorithm 2, Sec. 3.1) of `count`
+ * problems of the same degree k, batched (the merged launches have no
+ * counterpart in the paper, which smooths one problem): per colour, every problem's colour residual, then ONE launch of
  * the patch kernel over that colour's patches of all the problems (64
  * problems per launch).  levels[i]: the level smoothed in problem i; x[i],
  * b[i]: its vectors, as in stk_smooth.  All work runs on problems[0]'s
@@ -225,7 +231,8 @@ int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve
 
 /* Solve `count` independent problems (each with its own setup, mesh, degree
  * and options) to ||b_i - A_i x_i|| <= rtol ||b_i||, by the same method as
- * stk_solve, with bitwise the same results.  The host interleaves the
+ * stk_solve (Sec. 3.3; batching has no counterpart in the paper), with
+ * bitwise the same results.  The host interleaves the
  * solves: it polls the problems' streams and, as soon as one has drained,
  * advances that problem's Krylov state and enqueues its next step, so
  * problems on distinct non-NULL streams run concurrently on the GPU (many
@@ -246,7 +253,7 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
 int stk_autotune(stk_problem* P, int dtype);
 
 /* The march length chosen by stk_autotune for a level and dtype (0 = not
- * tuned: the built-in choice is used). */
+ * tuned: the built-in choice is used); no counterpart in the paper. */
 int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_cta);
 
 /* b = right-hand side of a manufactured problem on the finest level

@@ -104,3 +104,18 @@ def test_c_program_sets_up_a_problem(tmp_path):
     exe = _build_c_program(tmp_path)
     r = subprocess.run([exe, "gpu"], capture_output=True, text=True)
     assert r.returncode == 0 and "layout n=4" in r.stdout, (r.returncode, r.stdout, r.stderr)
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration in include/*.h is preceded by a comment that cites the
+    passage of the paper defining the operation, or says it has none."""
+    missing = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        decls = re.finditer(r"/\*((?:(?!\*/).)*)\*/\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(stk_[A-Za-z0-9_]+)\s*\(", text, flags=re.S)
+        found = {}
+        for m in decls:
+            found[m.group(2)] = bool(re.search(r"Sec\.|eq\.|Algorithm|Table|no counterpart", m.group(1)))
+        missing += [n for n, ok in found.items() if not ok]
+        missing += [n for n in declared_symbols() if n not in found and os.path.basename(h) == "stokesmg.h"]
+    assert not missing, missing
