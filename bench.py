@@ -45,6 +45,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the velocity
+# kernel, keyed by (k, n, dtype): one ncu capture on 48^3 cells scaled to the
+# benchmarked mesh by velocity DoFs (profiles/apply_velocity_f64_k3_n48_ncu_full.md).
+# Valid only for the kernel version it was taken on; other keys report null.
+DRAM_TRAFFIC = {(3, 64, "f64"): 1249000000}
+
+
 def velocity_flops_per_dof(k: int) -> float:
     """Algorithmic flops of the velocity rows per velocity DoF (Kronecker form, cell-local).
 
@@ -622,11 +629,7 @@ def run_ours(args):
     vflops = velocity_flops_per_dof(k) * 3 * nv
     alu_peak = FP64_PEAK_TFLOPS if dt == torch.float64 else FP32_PEAK_TFLOPS
     achieved_tf = vflops / t_vel / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    key = f"apply_velocity_k{k}_n{n}_{args.dtype}"
-    if os.path.exists(tpath):
-        traffic = json.load(open(tpath)).get(key)
+    traffic = DRAM_TRAFFIC.get((k, n, args.dtype))
     apply_bytes = 2 * N * esize
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
