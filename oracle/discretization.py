@@ -14,7 +14,8 @@ Follows Sec. 2.1 of the paper:
     `average`.  The whole viscous form is multiplied by the viscosity nu.
   * divergence blocks: eq. `weak_form` together with Algorithm 1 (d) and the
     symmetric block form of eq. `block_A`: velocity rows get
-    +(p, div v), pressure rows get +(q, div u) (a reading).
+    +(p, div v), pressure rows get +(q, div u) (a reading: two of the three
+    passages use the symmetric form; the discrete pressure then approximates -p).
   * penalty: gamma = penalty_factor * (k+1)(k+2) / h (the paper leaves
     gamma_e undefined; a reading).
   * quadrature: (k+3)-point Gauss rule per direction, exact for every

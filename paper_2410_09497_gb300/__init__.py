@@ -67,7 +67,7 @@ def load_library():
         return _lib
     path = library_path()
     if not os.path.exists(path):
-        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() or python -m paper_2410_09497_gb300.build")
+        raise RuntimeError(f"{path} is missing: build it with python -m paper_2410_09497_gb300.build")
     lib = ctypes.CDLL(path)
     P = ctypes.c_void_p
     i64p = ctypes.POINTER(ctypes.c_int64)
