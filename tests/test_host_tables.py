@@ -80,3 +80,33 @@ def test_patch_eigen_rejects_invalid_arguments(binding):
     assert b"direction" in lib.stk_last_error(None)
     assert lib.stk_patch_eigen(4, 2, 1.0, 1.0, 0, None, lam.ctypes.data, ctypes.byref(d), ctypes.byref(e)) == -1
     assert args(4, 2, 1.0, 1.0, 1) == 0 and d.value == 6
+
+
+def _type_direction(vertex_index, n):
+    """stk_patch_eigen direction of a discontinuous direction from the patch's
+    position: 1 + (lower cell on the mesh boundary) + 2 (upper cell on it)."""
+    return 1 + (1 if vertex_index == 1 else 0) + (2 if vertex_index == n - 1 else 0)
+
+
+@pytest.mark.parametrize("n,k,vertex,nu", [(4, 1, (2, 2, 2), 1.0), (4, 2, (3, 1, 2), 1.0), (4, 3, (2, 1, 3), 2.5), (2, 2, (1, 1, 1), 1.0), (3, 2, (1, 2, 1), 0.7)])
+def test_fdm_inverse_equals_the_oracle_patch_block(binding, n, k, vertex, nu):
+    """Sec. 3.2, eq. `fast_inverse`: with the library's 1D eigenpairs of the
+    patch's boundary types, (S_z (x) S_y (x) S_x) diag(1 / nu (l_z + l_y + l_x))
+    (S_z (x) S_y (x) S_x)^T is the inverse of the u_x block of the patch matrix
+    that the oracle assembles by quadrature."""
+    from oracle.discretization import Discretization
+    from oracle.multigrid import patch_dofs
+
+    d = Discretization(n, k, nu)
+    J = patch_dofs(d, vertex)
+    n0 = (2 * k + 1) * (2 * k + 2) ** 2
+    Au = d.assemble()[J[:n0]][:, J[:n0]].toarray()
+    Sx, lx, _ = binding.patch_eigen(n, k, 0, nu=nu)
+    Sy, ly, _ = binding.patch_eigen(n, k, _type_direction(vertex[1], n), nu=nu)
+    Sz, lz, _ = binding.patch_eigen(n, k, _type_direction(vertex[2], n), nu=nu)
+    S = np.kron(Sz, np.kron(Sy, Sx))
+    lam = nu * np.add.outer(np.add.outer(lz, ly), lx).reshape(-1)
+    r = np.random.default_rng(41).standard_normal(n0)
+    fdm = S @ ((S.T @ r) / lam)
+    ref = np.linalg.solve(Au, r)
+    assert np.abs(fdm - ref).max() <= 1e-11 * np.abs(ref).max()
