@@ -90,23 +90,30 @@ def _type_direction(vertex_index, n):
 
 @pytest.mark.parametrize("n,k,vertex,nu", [(4, 1, (2, 2, 2), 1.0), (4, 2, (3, 1, 2), 1.0), (4, 3, (2, 1, 3), 2.5), (2, 2, (1, 1, 1), 1.0), (3, 2, (1, 2, 1), 0.7)])
 def test_fdm_inverse_equals_the_oracle_patch_block(binding, n, k, vertex, nu):
-    """Sec. 3.2, eq. `fast_inverse`: with the library's 1D eigenpairs of the
-    patch's boundary types, (S_z (x) S_y (x) S_x) diag(1 / nu (l_z + l_y + l_x))
-    (S_z (x) S_y (x) S_x)^T is the inverse of the u_x block of the patch matrix
-    that the oracle assembles by quadrature."""
+    """Sec. 3.2, eq. `fast_inverse`: for each velocity component c, with the
+    library's 1D eigenpairs (the continuous direction c, and the patch's
+    boundary types in the other two), (S_z (x) S_y (x) S_x)
+    diag(1 / nu (l_z + l_y + l_x)) (S_z (x) S_y (x) S_x)^T is the inverse of
+    the u_c block of the patch matrix that the oracle assembles by quadrature."""
     from oracle.discretization import Discretization
     from oracle.multigrid import patch_dofs
 
     d = Discretization(n, k, nu)
+    A = d.assemble()
     J = patch_dofs(d, vertex)
     n0 = (2 * k + 1) * (2 * k + 2) ** 2
-    Au = d.assemble()[J[:n0]][:, J[:n0]].toarray()
-    Sx, lx, _ = binding.patch_eigen(n, k, 0, nu=nu)
-    Sy, ly, _ = binding.patch_eigen(n, k, _type_direction(vertex[1], n), nu=nu)
-    Sz, lz, _ = binding.patch_eigen(n, k, _type_direction(vertex[2], n), nu=nu)
-    S = np.kron(Sz, np.kron(Sy, Sx))
-    lam = nu * np.add.outer(np.add.outer(lz, ly), lx).reshape(-1)
-    r = np.random.default_rng(41).standard_normal(n0)
-    fdm = S @ ((S.T @ r) / lam)
-    ref = np.linalg.solve(Au, r)
-    assert np.abs(fdm - ref).max() <= 1e-11 * np.abs(ref).max()
+    rng = np.random.default_rng(41)
+    for c in range(3):
+        Jc = J[c * n0:(c + 1) * n0]
+        Au = A[Jc][:, Jc].toarray()
+        S1, l1 = [], []
+        for dirn in range(3):  # x, y, z
+            S_d, l_d, _ = binding.patch_eigen(n, k, 0 if dirn == c else _type_direction(vertex[dirn], n), nu=nu)
+            S1.append(S_d)
+            l1.append(l_d)
+        S = np.kron(S1[2], np.kron(S1[1], S1[0]))
+        lam = nu * np.add.outer(np.add.outer(l1[2], l1[1]), l1[0]).reshape(-1)
+        r = rng.standard_normal(n0)
+        fdm = S @ ((S.T @ r) / lam)
+        ref = np.linalg.solve(Au, r)
+        assert np.abs(fdm - ref).max() <= 1e-11 * np.abs(ref).max(), c
