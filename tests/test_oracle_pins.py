@@ -23,6 +23,19 @@ from seeded_inputs import manufactured_coefficients, random_vector
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
 
 
+# ------------------------------------------------------------ seeded inputs
+def test_splitmix64_reference_outputs():
+    """splitmix64 (Steele, Lea, Flood 2014) from state 0: the first outputs of
+    the published generator are e220a8397b1dcdaf, 6e789e6aa1b965f4,
+    06c45d188009454f; uniform draws use the top 53 bits."""
+    from seeded_inputs import splitmix64_stream, uniform_pm1
+
+    z = splitmix64_stream(0, 3)
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    u = uniform_pm1(0, 1)[0]
+    assert u == 2.0 * ((0xE220A8397B1DCDAF >> 11) / 2.0 ** 53) - 1.0
+
+
 # ----------------------------------------------------------------- 1D pieces
 def test_quadrature_closed_forms():
     x, w = gauss_lobatto(3)
