@@ -458,6 +458,24 @@ def test_convergence_divergence_and_flat_iterations():
     assert abs(its[1] - its[0]) <= 2
 
 
+@pytest.mark.slow
+def test_optimal_rates_k3():
+    """k = 3 on n = 4, 8 (about 80 s): L2 rates near k+1 = 4 for velocity and
+    pressure (observed 3.7 and 4.0; the 2 -> 4 step is still pre-asymptotic
+    for the pressure)."""
+    man = Manufactured(manufactured_coefficients(0))
+    errs = []
+    for n in (4, 8):
+        H = Hierarchy(n, 3)
+        d = H.levels[-1].disc
+        x, info = H.solve(rhs(d, man), tol=1e-12)
+        assert info["converged"]
+        errs.append(l2_errors(d, man, x))
+    ru = math.log2(errs[0][0] / errs[1][0])
+    rp = math.log2(errs[0][1] / errs[1][1])
+    assert ru > 3.4 and rp > 3.6, (ru, rp)
+
+
 def test_three_steps_for_k3():
     """Sec. 3.3: from k = 3 on, no more than three GMRES steps to 1e-8."""
     H = Hierarchy(4, 3)
