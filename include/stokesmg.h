@@ -270,9 +270,10 @@ int stk_rhs(stk_problem* P, const int* psi_freq, const double* psi_amp, const in
 
 /* stk_smooth without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that may not call cudaMalloc, such as
- * code recording into a CUDA graph (no allocation during stream capture), a
- * framework whose memory pool must own every device allocation, or a
- * real-time loop that cannot absorb an allocation stall.  Same kernels, same
+ * a framework whose memory pool must own every device allocation (a foreign
+ * cudaMalloc escapes its accounting and can fail once the pool holds the
+ * memory), or a real-time loop that cannot absorb the device synchronisation
+ * a cudaMalloc may cause.  Same kernels, same
  * order and same result as stk_smooth; the colour residual lives in a 32 MiB
  * array of device global memory built into the library (every GPU that loads
  * the library holds it until exit), so the level must have

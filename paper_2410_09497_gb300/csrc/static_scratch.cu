@@ -1,11 +1,12 @@
 // A variant of the patch smoother that allocates no device memory.
 //
 // stk_smooth keeps its per-colour residual in workspace that the library
-// allocates with cudaMalloc on first use.  Some callers cannot allow that: an
-// application that records its work into a CUDA graph (allocation is not
-// allowed while a stream is being captured), a framework that owns every
-// device allocation through its own pool and forbids others, or a real-time
-// host loop where a cudaMalloc stall is unacceptable.  stk_smooth_static
+// allocates with cudaMalloc on first use.  Some callers cannot allow that: a
+// framework that owns every device allocation through its own pool and
+// forbids others (a foreign cudaMalloc would escape its accounting and could
+// fail once the pool has taken the memory), or a real-time host loop where a
+// cudaMalloc, which may synchronise the device, is an unacceptable stall.
+// stk_smooth_static
 // runs the same kernels in the same order, with the residual held in one
 // fixed array in device global memory that is part of the library image.
 //

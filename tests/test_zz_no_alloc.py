@@ -1,7 +1,8 @@
 """stk_smooth_static: the smoother variant that allocates no device memory.
 
-Callers that may not allocate (graph capture, a framework-owned memory pool,
-real-time loops) use it in place of stk_smooth.  It must give the same result
+Callers that may not allocate (a framework whose memory pool owns every
+device allocation, a real-time loop that cannot absorb a cudaMalloc stall) use
+it in place of stk_smooth.  It must give the same result
 as stk_smooth, call after call, although every call reuses the same static
 residual array.  This file is collected last on purpose.
 """
