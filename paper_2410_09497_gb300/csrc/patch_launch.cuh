@@ -1,0 +1,49 @@
+// Definitions of the patch-kernel launchers, instantiated for one degree
+// (both precisions) by each patch_k<K>.cu.
+#pragma once
+
+#include "patch_kernel.cuh"
+
+namespace stk {
+
+template <int K, typename T>
+cudaError_t launch_patch_k(PatchArgs<T> a, int nblocks, cudaStream_t s) {
+  using C = PatchCfg<K>;
+  const size_t smem = patch_smem_bytes<K>(sizeof(T));
+  static std::atomic<unsigned long long> smem_set{0}, smem_set_interior{0};
+  {
+    cudaError_t e = allow_dynamic_smem(patch_kernel<K, T>, smem, smem_set);
+    if (e == cudaSuccess) e = allow_dynamic_smem(patch_kernel_interior<K, T>, smem, smem_set_interior);
+    if (e != cudaSuccess) return e;
+  }
+  if (nblocks > 0) {
+    if (a.mode == 0 && a.part == 1)
+      patch_kernel_interior<K, T><<<nblocks, C::NT, smem, s>>>(a);
+    else
+      patch_kernel<K, T><<<nblocks, C::NT, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int K, typename T>
+cudaError_t launch_patch_multi_k(const PatchArgs<T>& a, const PatchJobs<T>& J, int nblocks, cudaStream_t s) {
+  using C = PatchCfg<K>;
+  const size_t smem = patch_smem_bytes<K>(sizeof(T));
+  static std::atomic<unsigned long long> smem_set{0};
+  {
+    const cudaError_t e = allow_dynamic_smem(patch_kernel_multi<K, T>, smem, smem_set);
+    if (e != cudaSuccess) return e;
+  }
+  if (nblocks > 0) patch_kernel_multi<K, T><<<nblocks, C::NT, smem, s>>>(a, J);
+  return cudaGetLastError();
+}
+
+#define STK_PATCH_INSTANTIATE(KK)                                                                       \
+  template cudaError_t launch_patch_k<KK, float>(PatchArgs<float>, int, cudaStream_t);                  \
+  template cudaError_t launch_patch_k<KK, double>(PatchArgs<double>, int, cudaStream_t);                \
+  template cudaError_t launch_patch_multi_k<KK, float>(const PatchArgs<float>&, const PatchJobs<float>&, \
+                                                       int, cudaStream_t);                              \
+  template cudaError_t launch_patch_multi_k<KK, double>(const PatchArgs<double>&,                      \
+                                                        const PatchJobs<double>&, int, cudaStream_t);
+
+}  // namespace stk
