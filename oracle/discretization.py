@@ -12,8 +12,8 @@ Follows Sec. 2.1 of the paper:
     - 2 <{{grad v}}, {{u (x) n}}>, boundary faces
     2 gamma <u, v> - <d_n u, v> - <u, d_n v>; {{.}} is the average of eq.
     `average`.  The whole viscous form is multiplied by the viscosity nu.
-  * divergence blocks: eq. `weak_form` together with Algorithm 1 (d) and the
-    symmetric block form of eq. `block_A`: velocity rows get
+  * divergence blocks: eq. `weak_form` together with the divergence term of
+    Algorithm 1 and the symmetric block form of eq. `block_A`: velocity rows get
     +(p, div v), pressure rows get +(q, div u) (a reading: two of the three
     passages use the symmetric form; the discrete pressure then approximates -p).
   * penalty: gamma = penalty_factor * (k+1)(k+2) / h (the paper leaves
