@@ -1,0 +1,186 @@
+"""Launch geometry and index maps of the CUDA kernels, checked on the CPU.
+
+compute-sanitizer is not available to these tests, so the index arithmetic of
+the two largest kernels is restated here and checked against the buffers it
+addresses and against the oracle's own numbering:
+
+* patch smoother (Algorithm 2): which patch a CTA takes in each of the three
+  launch kinds (every patch / interior patches / boundary patches), and the
+  global DoF of every patch-local unknown.  The restated map must give the
+  oracle's patch DoF set R_j in the same order, stay inside the vector, touch
+  no constrained boundary-normal DoF, and give disjoint sets to the patches of
+  one colour (the scatter x += R_j^T (U, P) has no atomics).
+* operator apply: the (tile, chunk) decomposition of the pencil march writes
+  every velocity entry exactly once, and the 32-bit per-CTA staging offsets
+  fit for every mesh the library accepts.
+"""
+import numpy as np
+import pytest
+
+from oracle.discretization import Discretization
+from oracle.multigrid import colour_vertices, patch_dofs
+
+# ---------------------------------------------------------------- patch kernel
+# Restated from the library: colour_counts, interior_box (smoother.cu), the
+# blk -> vertex decode and patch_node_global / patch_local_decode
+# (patch_kernel.cuh).
+
+
+def colour_counts(n, colour):
+    return [n // 2 if (colour >> d) & 1 else (n - 1) // 2 for d in range(3)]
+
+
+def interior_box(n, colour, cnt):
+    tlo, cint = [], []
+    for d in range(3):
+        bit = (colour >> d) & 1
+        lo, hi = cnt[d], 0
+        for t in range(cnt[d]):
+            v = 2 * t + 1 if bit else 2 * t + 2
+            if 2 <= v <= n - 2:
+                lo, hi = min(lo, t), max(hi, t + 1)
+        tlo.append(lo)
+        cint.append(max(0, hi - lo))
+    return tlo, cint
+
+
+def patch_of_block(blk, n, colour, part, cnt, tlo, cint):
+    """Vertex of CTA blk, or None where the boundary launch skips the patch."""
+    p, v = blk, []
+    for d in range(3):
+        ext = cint[d] if part == 1 else cnt[d]
+        t = (tlo[d] if part == 1 else 0) + p % ext
+        p //= ext
+        v.append(2 * t + 1 if (colour >> d) & 1 else 2 * t + 2)
+    interior = all(2 <= v[d] <= n - 2 for d in range(3))
+    if part == 2 and interior:
+        return None
+    return tuple(v)
+
+
+def patch_local_decode(j, k):
+    npc, npd = 2 * k + 1, 2 * k + 2
+    nv1 = npc * npd * npd
+    if j < 3 * nv1:
+        c = j // nv1
+        li = j - c * nv1
+        e0 = npc if c == 0 else npd
+        e1 = npc if c == 1 else npd
+        return c, li % e0, (li // e0) % e1, li // (e0 * e1)
+    q = j - 3 * nv1
+    return 3, q % npd, (q // npd) % npd, q // (npd * npd)
+
+
+def patch_node_global(c, i, v, k, m):
+    nd = k + 1
+    nvel = (m + 1) * m * m
+    g = [(v[d] - 1) * nd + i[d] + (1 if d == c else 0) for d in range(3)]
+    if c < 3:
+        e0 = m + 1 if c == 0 else m
+        e1 = m + 1 if c == 1 else m
+        return c * nvel + g[0] + e0 * (g[1] + e1 * g[2])
+    return 3 * nvel + g[0] + m * (g[1] + m * g[2])
+
+
+def patch_map(v, k, m):
+    npc, npd = 2 * k + 1, 2 * k + 2
+    nl = 3 * npc * npd * npd + npd ** 3
+    out = np.empty(nl, dtype=np.int64)
+    for j in range(nl):
+        c, i0, i1, i2 = patch_local_decode(j, k)
+        out[j] = patch_node_global(c, (i0, i1, i2), v, k, m)
+    return out
+
+
+@pytest.mark.parametrize("n,k", [(2, 1), (3, 2), (4, 1), (5, 3), (6, 2), (7, 1), (8, 2), (4, 5), (9, 1)])
+def test_patch_index_map_equals_the_oracle_patch_sets(n, k):
+    d = Discretization(n, k)
+    free = d.free_mask()
+    for colour in range(8):
+        cnt = colour_counts(n, colour)
+        tlo, cint = interior_box(n, colour, cnt)
+        every = [patch_of_block(b, n, colour, 0, cnt, tlo, cint) for b in range(int(np.prod(cnt)))]
+        inner = [patch_of_block(b, n, colour, 1, cnt, tlo, cint) for b in range(int(np.prod(cint)))]
+        outer = [patch_of_block(b, n, colour, 2, cnt, tlo, cint) for b in range(int(np.prod(cnt)))]
+        outer = [v for v in outer if v is not None]
+        expect = sorted(colour_vertices(n, colour))
+        assert sorted(every) == expect
+        # the split launches take every patch exactly once
+        assert sorted(inner + outer) == expect
+        assert all(2 <= v[e] <= n - 2 for v in inner for e in range(3))
+        seen = np.zeros(d.N, dtype=np.int32)
+        for v in every:
+            g = patch_map(v, k, d.m)
+            assert np.array_equal(g, patch_dofs(d, v)), (colour, v)
+            assert g.min() >= 0 and g.max() < d.N
+            assert free[g].all()
+            seen[g] += 1
+        assert seen.max() <= 1, f"patches of colour {colour} share a DoF"
+
+
+# ---------------------------------------------------------------- apply kernel
+# Restated from launch_apply_k (apply.cu): BJ cells per tile side, the march
+# length per CTA and the chunks of the continuous direction.
+
+BJ = {1: 8, 2: 5, 3: 4, 4: 3, 5: 2}
+
+
+def apply_grid(n, k, tuned=0):
+    nd = k + 1
+    m = n * nd
+    tj = BJ[k] * nd
+    ntile = (m + tj - 1) // tj
+    tiles = ntile * ntile
+    nch = (1216 + 3 * tiles - 1) // (3 * tiles)
+    nch = max(1, min(nch, n // 4 if n // 4 > 0 else 1))
+    chunk = min(tuned, n) if tuned > 0 else (n + nch - 1) // nch
+    nchunks = (n + chunk - 1) // chunk
+    return m, tj, ntile, chunk, nchunks
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n", [2, 3, 4, 6, 8, 12, 16, 24, 32])
+@pytest.mark.parametrize("tuned", [0, 1, 3, 7])
+def test_apply_march_writes_every_velocity_entry_once(n, k, tuned):
+    nd = k + 1
+    m, tj, ntile, chunk, nchunks = apply_grid(n, k, tuned)
+    # lines: the tiles cover [0, m)^2 with inactive threads past m
+    lines = np.zeros((m, m), dtype=np.int32)
+    for t in range(ntile * ntile):
+        j0, l0 = (t % ntile) * tj, (t // ntile) * tj
+        lines[j0:min(m, j0 + tj), l0:min(m, l0 + tj)] += 1
+    assert (lines == 1).all()
+    # along the continuous direction: the chunks' written nodes plus the top node
+    written = np.zeros(m + 1, dtype=np.int32)
+    for ch in range(nchunks):
+        cc0, cc1 = ch * chunk, min(n, ch * chunk + chunk)
+        cstart = cc0 - 1 if cc0 > 0 else 0
+        assert 0 <= cstart <= cc0 < cc1 <= n
+        for cc in range(cstart, cc1):
+            if cc < cc0:
+                continue  # carry-only step for the cell below the chunk
+            written[cc * nd: cc * nd + nd] += 1
+            if cc == n - 1:
+                written[m] += 1
+    assert (written == 1).all()
+
+
+def test_apply_staging_offsets_fit_in_32_bits():
+    # every mesh stk_setup accepts: n = 2^L or 3 * 2^L, n (k+1) <= 1200
+    sides = sorted({s << L for s in (2, 3) for L in range(12)})
+    for k in range(1, 6):
+        nd = k + 1
+        for n in sides:
+            m = n * nd
+            if m > 1200:
+                continue
+            for c in range(3):
+                e0 = m + 1 if c == 0 else m
+                e1 = m + 1 if c == 1 else m
+                sc = 1 if c == 0 else (e0 if c == 1 else e0 * e1)
+                d1 = 1 if c == 0 else 0
+                d2 = 1 if c == 2 else 2
+                s1 = 1 if d1 == 0 else e0
+                s2 = e0 if d2 == 1 else e0 * e1
+                # largest per-CTA offset of a staged element of cell 0
+                assert nd * sc + (m - 1) * s1 + (m - 1) * s2 < 2 ** 31, (n, k, c)
