@@ -13,6 +13,9 @@ addresses and against the oracle's own numbering:
 * operator apply: the (tile, chunk) decomposition of the pencil march writes
   every velocity entry exactly once, and the 32-bit per-CTA staging offsets
   fit for every mesh the library accepts.
+* level transfers: the prolongation's plain += reaches every free fine node
+  exactly once, and the restriction's atomic adds reach each coarse node at
+  most twice (two adds onto zero give the same sum in either order).
 """
 import numpy as np
 import pytest
@@ -184,3 +187,53 @@ def test_apply_staging_offsets_fit_in_32_bits():
                 s2 = e0 if d2 == 1 else e0 * e1
                 # largest per-CTA offset of a staged element of cell 0
                 assert nd * sc + (m - 1) * s1 + (m - 1) * s2 < 2 ** 31, (n, k, c)
+
+
+# ---------------------------------------------------------------- transfers
+# Restated from prolongate_add_kernel / restrict_kernel (transfer.cu): one CTA
+# per coarse cell; per field the fine nodes are the lower k+1 nodes of each of
+# the 8 children in every direction, the coarse nodes the cell's own nodes.
+
+
+def _field(f, m):
+    ext = [m + 1 if d == f else m for d in range(3)]
+    nvel = (m + 1) * m * m
+    return (f * nvel if f < 3 else 3 * nvel), (1, ext[0], ext[0] * ext[1]), (f if f < 3 else -1)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("nc", [1, 2, 3, 4])
+def test_transfer_index_maps(nc, k):
+    nd = k + 1
+    mc, mf = nc * nd, 2 * nc * nd
+    dc, df = Discretization(nc, k), Discretization(2 * nc, k)
+    fine_writes = np.zeros(df.N, dtype=np.int32)
+    coarse_adds = np.zeros(dc.N, dtype=np.int32)
+    a = np.arange(nd)
+    for cell in range(nc ** 3):
+        pc = (cell % nc, (cell // nc) % nc, cell // (nc * nc))
+        for f in range(4):
+            offc, stc, cdir = _field(f, mc)
+            offf, stf, _ = _field(f, mf)
+            # fine nodes: every child (ch0, ch1, ch2), lower nd nodes per direction
+            g = [np.add.outer(2 * pc[d] * nd + np.array([0, nd]), a).reshape(-1) for d in range(3)]
+            G2, G1, G0 = np.meshgrid(g[2], g[1], g[0], indexing="ij")
+            keep = np.ones(G0.shape, bool) if cdir < 0 else ((G0, G1, G2)[cdir] != 0)
+            idx = offf + G0 * stf[0] + G1 * stf[1] + G2 * stf[2]
+            fine_writes[idx[keep]] += 1  # each fine node appears once per CTA and field
+            # coarse nodes of the cell: nd per direction, nd + 1 along the continuous one
+            b = [pc[d] * nd + np.arange(nd + 1 if d == cdir else nd) for d in range(3)]
+            B2, B1, B0 = np.meshgrid(b[2], b[1], b[0], indexing="ij")
+            keep = np.ones(B0.shape, bool)
+            if cdir >= 0:
+                gcd = (B0, B1, B2)[cdir]
+                keep = (gcd != 0) & (gcd != mc)
+            cidx = offc + B0 * stc[0] + B1 * stc[1] + B2 * stc[2]
+            assert cidx.max() < dc.N and idx.max() < df.N
+            coarse_adds[cidx[keep]] += 1
+    free_f, free_c = df.free_mask(), dc.free_mask()
+    # prolongation: every free fine node written exactly once (plain +=, no race)
+    assert (fine_writes[free_f] == 1).all() and (fine_writes[~free_f] == 0).all()
+    # restriction: at most two atomic contributions onto zero (order independent)
+    assert (coarse_adds[free_c] >= 1).all() and coarse_adds.max() <= 2
+    assert (coarse_adds[~free_c] == 0).all()
