@@ -280,7 +280,7 @@ cudaError_t fill_factors(stk_problem* P, Coarse3Factors& F, unsigned char* flag)
 cudaError_t build_factors(stk_problem* P, Coarse3Factors& F) {
   const Level& L = P->levels[0];
   const cudaStream_t s = P->stream;
-  const int64_t nc = L.nvel, np = L.npress, N = L.ntotal;
+  const int64_t nc = L.nvel, np = L.npress;
   F.nc = nc;
   F.np = np;
   F.ldA = round_ld(nc);
