@@ -21,6 +21,7 @@
 // dense pseudo-inverse of the coarse problem at setup: on a 2^3 mesh the one
 // vertex patch holds every free DoF.  Two more kernels share the patch
 // solve: one for the interior patches of a large level (no dense transforms
+// compiled in) and one for a colour of several problems in one launch.
 //
 // Included by the patch_k<K>.cu files, one per degree, so that the
 // degrees compile in parallel, and by smoother.cu for the argument types
