@@ -101,7 +101,9 @@ int stk_default_options(stk_options* opt);
 /* Build the mesh hierarchy and the 1D tables of every level (Sec. 2.3,
  * Sec. 3.2) for the unit cube with n cells per side, degree k and viscosity
  * nu (Sec. 2, eq. `model` and eq. `weak_form`).  n must be 2 or 3 times a
- * power of two (n >= 2); k in 1..5; nu > 0.  opt may be NULL (defaults).  The
+ * power of two (n >= 2) with m = n (k+1) <= 1200 (larger meshes: STK_EINVAL,
+ * "mesh too large"; this keeps the operator's 32-bit per-CTA offsets in
+ * range); k in 1..5; nu > 0.  opt may be NULL (defaults).  The
  * multigrid workspace of a dtype, the coarse factors and the Krylov basis are
  * allocated by the first call that needs them.  On success *out owns device
  * memory until stk_destroy.  Synchronous. */
