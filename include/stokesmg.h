@@ -153,6 +153,29 @@ int stk_layout(const stk_problem* P, int level, int* n_cells, int64_t* n_vel_com
 int stk_patch_eigen(int n, int k, double nu, double penalty_factor, int direction, double* S, double* lambda,
                     int* dim, int* even_odd);
 
+/* The 1D cell matrices of the operator's Kronecker form (Sec. 2.3; the sums
+ * of Kronecker products that the operator apply evaluates), exactly as
+ * stk_setup builds them for a level of n cells per side, degree k, viscosity
+ * nu and penalty factor.  With nc = k+2 and nd = k+1 they are written, all
+ * row-major, one after another into the caller's host array out:
+ *   KC  nc x nc      nu times the stiffness of one cell's continuous
+ *                    (Gauss-Lobatto) basis;
+ *   MC  nc x nc      the mass of that basis;
+ *   D   nd x nc      D[a][i] = integral over the cell of psi_a phi_i', the
+ *                    divergence factor (psi: Gauss basis, phi: Lobatto basis);
+ *   LS  3 x nd x nd  diagonal block of nu times the 1D interior-penalty
+ *                    operator of a discontinuous direction (eq. `bilinear` on
+ *                    a line) for a cell inside the mesh (0), at its lower
+ *                    boundary (1) and at its upper boundary (2);
+ *   LLO nd x nd      its block coupling a cell's rows to the lower neighbour;
+ *   LHI nd x nd      its block coupling a cell's rows to the upper neighbour;
+ *   S   nd           the diagonal Gauss mass h w_a of a discontinuous direction;
+ * 2 nc^2 + nd nc + 5 nd^2 + nd doubles in all.  Host computation only: needs
+ * no GPU, touches no device and keeps no state.  STK_EINVAL (message in
+ * stk_last_error(NULL)) for k outside 1..5, n < 2, nu or penalty_factor not
+ * positive or out NULL; STK_ENOMEM if a host allocation fails. */
+int stk_cell_tables(int n, int k, double nu, double penalty_factor, double* out);
+
 /* y = A x on one level: the matrix-free Stokes operator of Algorithm 1 (cell,
  * interior-face and boundary-face loops of eq. `bilinear`, with the divergence
  * blocks of eq. `weak_form`), evaluated through its Kronecker form on the

@@ -11,7 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "patch_eigen", "solve_batch", "smooth_batch", "F64", "F32"]
+__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "patch_eigen", "cell_tables", "solve_batch", "smooth_batch", "F64", "F32"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBNAME = "libstokesmg.so"
@@ -94,6 +94,7 @@ def load_library():
         "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_smooth_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P)]),
         "stk_patch_eigen": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "stk_cell_tables": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -127,6 +128,28 @@ def patch_eigen(n: int, k: int, direction: int, nu: float = 1.0, penalty_factor:
         raise StokesError(rc, (lib.stk_last_error(None) or b"").decode())
     d = dim.value
     return S[: d * d].reshape(d, d).copy(), lam[:d].copy(), bool(eo.value)
+
+
+def cell_tables(n: int, k: int, nu: float = 1.0, penalty_factor: float = 1.0):
+    """The 1D cell matrices of stk_cell_tables as a dict of NumPy arrays
+    (KC, MC, D, LS with shape (3, k+1, k+1), LLO, LHI, S); host computation,
+    no GPU needed."""
+    import numpy as np
+
+    lib = load_library()
+    nc, nd = k + 2, k + 1
+    shapes = [("KC", (nc, nc)), ("MC", (nc, nc)), ("D", (nd, nc)), ("LS", (3, nd, nd)), ("LLO", (nd, nd)),
+              ("LHI", (nd, nd)), ("S", (nd,))]
+    buf = np.zeros(sum(int(np.prod(s)) for _, s in shapes))
+    rc = lib.stk_cell_tables(int(n), int(k), float(nu), float(penalty_factor), buf.ctypes.data)
+    if rc != 0:
+        raise StokesError(rc, (lib.stk_last_error(None) or b"").decode())
+    out, o = {}, 0
+    for name, s in shapes:
+        size = int(np.prod(s))
+        out[name] = buf[o:o + size].reshape(s).copy()
+        o += size
+    return out
 
 
 class StokesMG:

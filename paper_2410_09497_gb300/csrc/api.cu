@@ -113,6 +113,22 @@ int stk_default_options(stk_options* opt) {
   return STK_OK;
 }
 
+int stk_cell_tables(int n, int k, double nu, double penalty_factor, double* out) {
+  if (k < 1 || k > stk::kMaxDegree) return fail(nullptr, STK_EINVAL, "cell_tables: degree k must be in 1..5");
+  if (n < 2) return fail(nullptr, STK_EINVAL, "cell_tables: n must be at least 2");
+  if (!(nu > 0.0) || !(penalty_factor > 0.0))
+    return fail(nullptr, STK_EINVAL, "cell_tables: viscosity and penalty factor must be positive");
+  if (!out) return fail(nullptr, STK_EINVAL, "cell_tables: NULL output pointer");
+  try {
+    const stk::Tables1D t = stk::build_tables(k, 1.0 / n, nu, penalty_factor);
+    for (const std::vector<double>* v : {&t.KC, &t.MC, &t.D, &t.LS[0], &t.LS[1], &t.LS[2], &t.LLO, &t.LHI, &t.S})
+      out = std::copy(v->begin(), v->end(), out);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, STK_ENOMEM, "cell_tables: host allocation failed");
+  }
+  return STK_OK;
+}
+
 int stk_patch_eigen(int n, int k, double nu, double penalty_factor, int direction, double* S, double* lambda,
                     int* dim, int* even_odd) {
   if (k < 1 || k > stk::kMaxDegree) return fail(nullptr, STK_EINVAL, "patch_eigen: degree k must be in 1..5");

@@ -1,6 +1,7 @@
 """Host logic of the library, checked without a GPU: the 1D fast-diagonalization
 eigenpairs that stk_setup builds for the vertex-patch local solver (Sec. 3.2,
-eq. `inverse2d`, eq. `fast_inverse`), read through stk_patch_eigen.
+eq. `inverse2d`, eq. `fast_inverse`), read through stk_patch_eigen, and the 1D
+cell matrices of the operator apply (Sec. 2.3), read through stk_cell_tables.
 
 The 1D patch operators are taken as principal submatrices of global 1D
 matrices assembled independently in tests/test_oracle_pins.py (its Kronecker
@@ -117,3 +118,79 @@ def test_fdm_inverse_equals_the_oracle_patch_block(binding, n, k, vertex, nu):
         fdm = S @ ((S.T @ r) / lam)
         ref = np.linalg.solve(Au, r)
         assert np.abs(fdm - ref).max() <= 1e-11 * np.abs(ref).max(), c
+
+
+# ------------------------------------------------------------ operator tables
+# The 1D cell matrices of the operator apply (Sec. 2.3), read through
+# stk_cell_tables, assembled into global 1D matrices and compared with the
+# independent 1D assembly of tests/test_oracle_pins.py (whose Kronecker sum
+# equals the oracle's literal assembly of eq. `bilinear`).
+
+
+def _assemble_from_cells(t, n, k):
+    nc, nd = k + 2, k + 1
+    m = n * nd
+    KC = np.zeros((m + 1, m + 1))
+    MC = np.zeros((m + 1, m + 1))
+    D = np.zeros((m, m + 1))
+    L = np.zeros((m, m))
+    for c in range(n):
+        ic = c * nd + np.arange(nc)
+        idd = c * nd + np.arange(nd)
+        KC[np.ix_(ic, ic)] += t["KC"]
+        MC[np.ix_(ic, ic)] += t["MC"]
+        D[np.ix_(idd, ic)] += t["D"]
+        L[np.ix_(idd, idd)] += t["LS"][1 if c == 0 else (2 if c == n - 1 else 0)]
+        if c > 0:
+            L[np.ix_(idd, idd - nd)] += t["LLO"]
+        if c < n - 1:
+            L[np.ix_(idd, idd + nd)] += t["LHI"]
+    return KC, MC, D, L, np.diag(np.tile(t["S"], n))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n,nu,pf", [(2, 1.0, 1.0), (3, 0.5, 2.0), (5, 2.0, 1.0)])
+def test_cell_tables_assemble_to_the_global_1d_operators(binding, n, k, nu, pf):
+    # n = 2 has no interior cell; LS[0] is checked by n = 3 and 5
+    t = binding.cell_tables(n, k, nu=nu, penalty_factor=pf)
+    gamma = pf * (k + 1) * (k + 2) * n
+    LC, MC, Dv, LD, MD = _one_d(n, k, 1.0, gamma)
+    KCg, MCg, Dg, Lg, Sg = _assemble_from_cells(t, n, k)
+    rel = lambda a, b: np.abs(a - b).max() / np.abs(b).max()
+    assert rel(KCg, nu * LC) < 1e-12
+    assert rel(MCg, MC) < 1e-12
+    assert rel(Dg, Dv) < 1e-12
+    assert rel(Lg, nu * LD) < 1e-12
+    assert rel(Sg, MD) < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_cell_tables_reflection_symmetry(binding, k):
+    """The node sets are symmetric under the cell's reflection, so KC, MC and
+    the interior penalty block are centro-symmetric, D is antisymmetric, the
+    two boundary blocks and the two coupling blocks are each other's
+    reflections, and the Gauss mass is symmetric: the structure an even-odd
+    evaluation of the apply uses."""
+    t = binding.cell_tables(4, k, nu=1.3, penalty_factor=1.0)
+    R = lambda a: a[::-1, ::-1]
+    close = lambda a, b: np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    assert close(R(t["KC"]), t["KC"]) and close(R(t["MC"]), t["MC"])
+    assert close(R(t["LS"][0]), t["LS"][0]) and close(R(t["LS"][1]), t["LS"][2])
+    assert close(R(t["LLO"]), t["LHI"])
+    assert close(R(t["D"]), -t["D"])
+    assert close(t["S"][::-1], t["S"])
+
+
+def test_cell_tables_rejects_invalid_arguments(binding):
+    import ctypes
+
+    lib = binding.load_library()
+    buf = np.zeros(1024)
+    assert lib.stk_cell_tables(4, 0, 1.0, 1.0, buf.ctypes.data) == -1
+    assert lib.stk_cell_tables(4, 6, 1.0, 1.0, buf.ctypes.data) == -1
+    assert lib.stk_cell_tables(1, 2, 1.0, 1.0, buf.ctypes.data) == -1
+    assert lib.stk_cell_tables(4, 2, 0.0, 1.0, buf.ctypes.data) == -1
+    assert lib.stk_cell_tables(4, 2, 1.0, -1.0, buf.ctypes.data) == -1
+    assert lib.stk_cell_tables(4, 2, 1.0, 1.0, None) == -1
+    assert b"cell_tables" in lib.stk_last_error(None)
+    assert lib.stk_cell_tables(4, 2, 1.0, 1.0, ctypes.c_void_p(buf.ctypes.data)) == 0
