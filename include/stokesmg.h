@@ -176,6 +176,20 @@ int stk_patch_eigen(int n, int k, double nu, double penalty_factor, int directio
  * positive or out NULL; STK_ENOMEM if a host allocation fails. */
 int stk_cell_tables(int n, int k, double nu, double penalty_factor, double* out);
 
+/* The 1D child matrices of the level transfers (Sec. 3: the prolongation is
+ * the canonical embedding of the nested spaces, the restriction its
+ * transpose) exactly as stk_setup builds them for degree k: with nc = k+2,
+ * nd = k+1 and zC / zD the Gauss-Lobatto / Gauss points of [0, 1],
+ *   PC[ch][a][b] = lC_b((ch + zC_a) / 2)   ch = 0, 1; a, b < nc
+ *   PD[ch][a][b] = lD_b((ch + zD_a) / 2)   ch = 0, 1; a, b < nd
+ * (lC, lD the Lagrange bases of a coarse cell; ch the child, a the child's
+ * node, b the coarse node), written row-major into the caller's host array
+ * out, PC first: 2 nc^2 + 2 nd^2 doubles.  Host computation only: needs no
+ * GPU, touches no device and keeps no state.  STK_EINVAL (message in
+ * stk_last_error(NULL)) for k outside 1..5 or out NULL; STK_ENOMEM if a host
+ * allocation fails. */
+int stk_transfer_tables(int k, double* out);
+
 /* y = A x on one level: the matrix-free Stokes operator of Algorithm 1 (cell,
  * interior-face and boundary-face loops of eq. `bilinear`, with the divergence
  * blocks of eq. `weak_form`), evaluated through its Kronecker form on the

@@ -11,7 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "patch_eigen", "cell_tables", "solve_batch", "smooth_batch", "F64", "F32"]
+__all__ = ["StokesMG", "load_library", "library_path", "StokesError", "layout_sizes", "patch_eigen", "cell_tables", "transfer_tables", "solve_batch", "smooth_batch", "F64", "F32"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBNAME = "libstokesmg.so"
@@ -95,6 +95,7 @@ def load_library():
         "stk_smooth_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P)]),
         "stk_patch_eigen": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "stk_cell_tables": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, P]),
+        "stk_transfer_tables": (ctypes.c_int, [ctypes.c_int, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -150,6 +151,20 @@ def cell_tables(n: int, k: int, nu: float = 1.0, penalty_factor: float = 1.0):
         out[name] = buf[o:o + size].reshape(s).copy()
         o += size
     return out
+
+
+def transfer_tables(k: int):
+    """(PC, PD) of stk_transfer_tables as NumPy arrays of shape (2, k+2, k+2)
+    and (2, k+1, k+1); host computation, no GPU needed."""
+    import numpy as np
+
+    lib = load_library()
+    nc, nd = k + 2, k + 1
+    buf = np.zeros(2 * nc * nc + 2 * nd * nd)
+    rc = lib.stk_transfer_tables(int(k), buf.ctypes.data)
+    if rc != 0:
+        raise StokesError(rc, (lib.stk_last_error(None) or b"").decode())
+    return buf[: 2 * nc * nc].reshape(2, nc, nc).copy(), buf[2 * nc * nc:].reshape(2, nd, nd).copy()
 
 
 class StokesMG:

@@ -129,6 +129,18 @@ int stk_cell_tables(int n, int k, double nu, double penalty_factor, double* out)
   return STK_OK;
 }
 
+int stk_transfer_tables(int k, double* out) {
+  if (k < 1 || k > stk::kMaxDegree) return fail(nullptr, STK_EINVAL, "transfer_tables: degree k must be in 1..5");
+  if (!out) return fail(nullptr, STK_EINVAL, "transfer_tables: NULL output pointer");
+  try {
+    const std::vector<double> t = stk::build_transfer_tables(k);
+    std::copy(t.begin(), t.end(), out);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, STK_ENOMEM, "transfer_tables: host allocation failed");
+  }
+  return STK_OK;
+}
+
 int stk_patch_eigen(int n, int k, double nu, double penalty_factor, int direction, double* S, double* lambda,
                     int* dim, int* even_odd) {
   if (k < 1 || k > stk::kMaxDegree) return fail(nullptr, STK_EINVAL, "patch_eigen: degree k must be in 1..5");

@@ -12,6 +12,7 @@ after.
 """
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from test_oracle_pins import _one_d
 
@@ -194,3 +195,58 @@ def test_cell_tables_rejects_invalid_arguments(binding):
     assert lib.stk_cell_tables(4, 2, 1.0, 1.0, None) == -1
     assert b"cell_tables" in lib.stk_last_error(None)
     assert lib.stk_cell_tables(4, 2, 1.0, 1.0, ctypes.c_void_p(buf.ctypes.data)) == 0
+
+
+# ------------------------------------------------------------ transfer tables
+# The 1D child matrices of the level transfers (Sec. 3), read through
+# stk_transfer_tables, put together the way the transfer kernels use them (a
+# fine node is the lower k+1 nodes of a child along every direction; the
+# upper end node of the continuous direction is a constrained boundary node)
+# must give the oracle's prolongation matrix, built by evaluating the coarse
+# basis at every fine support point.
+
+
+def _prolongation_from_tables(PC, PD, nc_cells, k):
+    nd = k + 1
+    mc, mf = nc_cells * nd, 2 * nc_cells * nd
+    P1 = {}
+    for cont, T, ext_c, ext_f in ((True, PC, mc + 1, mf + 1), (False, PD, mc, mf)):
+        M = np.zeros((ext_f, ext_c))
+        nb = T.shape[2]
+        for c in range(nc_cells):
+            for ch in range(2):
+                for a in range(nd):
+                    M[(2 * c + ch) * nd + a, c * nd + np.arange(nb)] = T[ch, a]
+        P1[cont] = M
+    blocks = []
+    for comp in range(4):
+        f = [P1[d == comp] for d in range(3)]
+        blocks.append(sp.kron(sp.kron(sp.csr_matrix(f[2]), sp.csr_matrix(f[1])), sp.csr_matrix(f[0])))
+    return sp.block_diag(blocks).tocsr()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("nc_cells", [1, 2, 3])
+def test_transfer_tables_give_the_oracle_embedding(binding, nc_cells, k):
+    from oracle.discretization import Discretization
+    from oracle.transfer import prolongation
+
+    PC, PD = binding.transfer_tables(k)
+    coarse, fine = Discretization(nc_cells, k), Discretization(2 * nc_cells, k)
+    Po = prolongation(coarse, fine).tocsr()
+    Pt = _prolongation_from_tables(PC, PD, nc_cells, k)
+    ff, fc = fine.free_mask(), coarse.free_mask()
+    diff = (Pt - Po)[ff][:, fc]
+    assert diff.nnz == 0 or np.abs(diff.data).max() < 1e-13 * np.abs(Po.data).max()
+    # the oracle's rows and columns of constrained DoFs are zero
+    assert Po[~ff].nnz == 0 or not Po[~ff].data.any()
+    assert Po[:, ~fc].nnz == 0 or not Po[:, ~fc].data.any()
+
+
+def test_transfer_tables_reject_invalid_arguments(binding):
+    lib = binding.load_library()
+    buf = np.zeros(512)
+    assert lib.stk_transfer_tables(0, buf.ctypes.data) == -1
+    assert lib.stk_transfer_tables(6, buf.ctypes.data) == -1
+    assert lib.stk_transfer_tables(3, None) == -1
+    assert b"transfer_tables" in lib.stk_last_error(None)
