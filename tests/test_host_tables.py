@@ -1,7 +1,9 @@
 """Host logic of the library, checked without a GPU: the 1D fast-diagonalization
 eigenpairs that stk_setup builds for the vertex-patch local solver (Sec. 3.2,
-eq. `inverse2d`, eq. `fast_inverse`), read through stk_patch_eigen, and the 1D
-cell matrices of the operator apply (Sec. 2.3), read through stk_cell_tables.
+eq. `inverse2d`, eq. `fast_inverse`), read through stk_patch_eigen, the 1D
+cell matrices of the operator apply (Sec. 2.3), read through stk_cell_tables,
+and the 1D child matrices of the level transfers (Sec. 3), read through
+stk_transfer_tables.
 
 The 1D patch operators are taken as principal submatrices of global 1D
 matrices assembled independently in tests/test_oracle_pins.py (its Kronecker
