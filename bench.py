@@ -46,9 +46,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the velocity
-# kernel, keyed by (k, n, dtype): one ncu capture on 48^3 cells scaled to the
-# benchmarked mesh by velocity DoFs (profiles/apply_velocity_f64_k3_n48_ncu_full.md).
-# Valid only for the kernel version it was taken on; other keys report null.
+# kernel, keyed by (k, n, dtype): one ncu capture of a single launch on 48^3
+# cells (x larger than L2), scaled to the benchmarked mesh by its velocity
+# DoFs.  Valid only for the kernel version it was taken on; other keys report
+# null.
 DRAM_TRAFFIC = {(3, 64, "f64"): 1249000000}
 
 
@@ -195,28 +196,84 @@ def whole_job_rate(units_per_rank: int, ws: int, steps: int, seconds: float) -> 
     return units_per_rank * ws * steps / seconds
 
 
-def oracle_spmv_rate(n: int, k: int, min_seconds: float, reps_per_step: int = 0):
-    """CSR SpMV of the oracle's assembled matrix on an n^3 sample; returns DoF/s and details."""
-    from oracle.discretization import Discretization
-    from seeded_inputs import random_vector
+class OracleSpMV:
+    """The oracle's assembled CSR matrix on an n^3 sample and its product with
+    a seeded vector, on `threads` host threads: row blocks of the same matrix
+    multiplied concurrently (SciPy's CSR product releases the GIL), the
+    oracle's own arithmetic in every block."""
 
-    d = Discretization(n, k)
-    A = d.assemble()
-    x = random_vector(1001, d.N) * d.free_mask()
-    y = A @ x
-    reps = 0
-    t0 = time.perf_counter()
-    while True:
-        y = A @ x
-        reps += 1
-        if (reps_per_step and reps >= reps_per_step) or (not reps_per_step and time.perf_counter() - t0 >= min_seconds):
-            break
-    dt = time.perf_counter() - t0
-    return d.N * reps / dt, {"n": n, "k": k, "dofs": d.N, "reps": reps, "seconds": dt}
+    def __init__(self, n: int, k: int, threads: int = 1):
+        from concurrent.futures import ThreadPoolExecutor
+
+        import numpy as np
+
+        from oracle.discretization import Discretization
+        from seeded_inputs import random_vector
+
+        d = Discretization(n, k)
+        self.n, self.k, self.N = n, k, d.N
+        self.A = d.assemble()
+        self.x = random_vector(1001, d.N) * d.free_mask()
+        self.threads = max(1, int(threads))
+        cut = np.linspace(0, d.N, self.threads + 1).astype(np.int64)
+        self.blocks = [(cut[i], cut[i + 1], self.A[cut[i]:cut[i + 1]]) for i in range(self.threads)]
+        self.y = np.empty(d.N)
+        self.pool = ThreadPoolExecutor(self.threads) if self.threads > 1 else None
+
+    def _block(self, i):
+        lo, hi, Ab = self.blocks[i]
+        self.y[lo:hi] = Ab @ self.x
+
+    def spmv(self):
+        if self.pool is None:
+            self.y[:] = self.A @ self.x
+        else:
+            list(self.pool.map(self._block, range(self.threads)))
+
+    def rate(self, min_seconds: float):
+        """DoF/s over repeated products for at least min_seconds."""
+        self.spmv()
+        reps = 0
+        t0 = time.perf_counter()
+        while True:
+            self.spmv()
+            reps += 1
+            if time.perf_counter() - t0 >= min_seconds:
+                break
+        dt = time.perf_counter() - t0
+        return self.N * reps / dt, {"n": self.n, "k": self.k, "dofs": self.N, "reps": reps, "seconds": dt,
+                                    "threads": self.threads}
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.shutdown()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_spmv_baselines(n: int, k: int, seconds: float):
+    """cpu_baseline objects of the oracle's SpMV on all host cores and on one."""
+    out = {}
+    for name, threads in (("all", host_cores()), ("one", 1)):
+        o = OracleSpMV(n, k, threads)
+        rate, info = o.rate(seconds)
+        o.close()
+        out[name] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": info["threads"], "kind": "oracle",
+                     "sample": f"CSR SpMV of the oracle's assembled matrix on {info['n']}^3 cells, k={k} "
+                               f"({info['dofs']} DoF), {info['threads']} thread(s) over row blocks, "
+                               f"{info['reps']} SpMVs in {info['seconds']:.1f} s"}
+    return out
 
 
 def oracle_solve_rate(n: int, k: int):
-    """The oracle's FGMRES + V-cycle solve (dense-LU patch solves) to 1e-8 on an n^3 sample."""
+    """The oracle's FGMRES + V-cycle solve to 1e-8 on an n^3 sample, with the
+    Schur-complement local solver (15 CG steps with dense-Cholesky velocity
+    solves), the GPU solve's local solver; single-threaded."""
     from oracle.manufactured import Manufactured, rhs
     from oracle.multigrid import Hierarchy
     from seeded_inputs import manufactured_coefficients
@@ -252,15 +309,19 @@ def run_solve_pair(args, stream, ws):
             x = torch.zeros_like(b)
             P.rhs(coef, b)
             P.solve(b, x, 1e-8)  # warm-up: workspace, coarse pseudo-inverse
-            torch.cuda.synchronize()
-            barrier(ws)
-            t0 = time.perf_counter()
-            info = P.solve(b, x, 1e-8)
-            torch.cuda.synchronize()
-            t = max_over_ranks(ws, time.perf_counter() - t0)
+            times = []
+            for _ in range(max(1, args.solve_reps)):
+                torch.cuda.synchronize()
+                barrier(ws)
+                t0 = time.perf_counter()
+                info = P.solve(b, x, 1e-8)
+                torch.cuda.synchronize()
+                times.append(max_over_ranks(ws, time.perf_counter() - t0))
             P.close()
+        t = statistics.median(times)
         out[name] = {"seconds": t, "s_per_MDoF": t / (N / 1e6), "dofs": N, "iterations": info["iterations"],
-                     "nu": info["nu"], "relres": info["relres"], "converged": info["converged"]}
+                     "nu": info["nu"], "relres": info["relres"], "converged": info["converged"],
+                     "timed_solves": len(times), "seconds_min": min(times), "seconds_max": max(times)}
     out["mixed_speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     out["mixed_speedup_direct"] = out["fp64_direct"]["seconds"] / out["mixed_direct"]["seconds"]
     out["local_solvers"] = ("mixed / fp64: Schur-complement CG, 15 steps (the paper's method); "
@@ -524,33 +585,36 @@ def run_solve_mode(args):
 
 
 def run_reference(args):
-    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    """The reference arm: the CPU oracle's assembled-matrix SpMV (the operator
+    apply as a plain CSR product) on all host cores, each step `ref_reps`
+    products on an 8^3-cell sample of the benchmarked workload (the 64^3
+    matrix would not fit a host: about 75 GB of CSR)."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     sample_n, k = 8, args.k
-    from oracle.discretization import Discretization
-    from seeded_inputs import random_vector
-
-    d = Discretization(sample_n, k)
-    A = d.assemble()
-    x = random_vector(1001, d.N) * d.free_mask()
+    o = OracleSpMV(sample_n, k, host_cores())
     reps = args.ref_reps
     for _ in range(args.warmup):
         for _ in range(reps):
-            A @ x
+            o.spmv()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         for _ in range(reps):
-            A @ x
+            o.spmv()
     dt = time.perf_counter() - t0
-    rate = d.N * reps * args.steps / dt / 1e9
+    o.close()
+    rate = o.N * reps * args.steps / dt / 1e9
+    sample = (f"CSR SpMV of the oracle's assembled matrix, {sample_n}^3 cells k={k} ({o.N} DoF), "
+              f"{reps} SpMVs per step, {o.threads} threads over row blocks")
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "GDoF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"FP64 Stokes apply, RT_{k} x DGQ_{k}, {args.n}^3 cells", "n": args.n, "k": k},
-        "cpu_baseline": {"value": rate, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-                         "sample": f"CSR SpMV of the oracle's assembled matrix, {sample_n}^3 cells k={k} ({d.N} DoF), {reps} SpMVs per step"},
+        "config": {"workload": f"FP64 Stokes apply, RT_{k} x DGQ_{k}, CPU oracle on a {sample_n}^3-cell sample "
+                               f"of the {args.n}^3-cell workload", "n": sample_n, "k": k, "dofs": o.N,
+                   "sample_of_n": args.n},
+        "cpu_baseline": {"value": rate, "unit": "GDoF/s", "cores": o.threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -641,7 +705,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "apply_velocity_kernel", "achieved": achieved_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak, "traffic": traffic,
                      "peak_source": "derived: 152 SMs x %s FMA/clk x 2 x 2.07 GHz" % ("2 FP64" if esize == 8 else "128 FP32"),
-                     "ms_per_launch": t_vel * 1e3, "flop_per_launch": vflops},
+                     "ms_per_launch": t_vel * 1e3, "flop_per_launch": vflops,
+                     "flop_per_velocity_dof": velocity_flops_per_dof(k),
+                     "frac_at_8k_plus_14_fma": 2 * (8 * k + 14) * 3 * nv / t_vel / 1e12 / alu_peak},
         "hbm_roofline": {"achieved_gbs": apply_bytes * K / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
                          "frac": apply_bytes * K / t / 1e9 / hbm_peak, "peak_source": peak_src,
                          "bytes_per_step": apply_bytes},
@@ -659,9 +725,9 @@ def run_ours(args):
     if args.batch > 0:
         line["batch"] = run_batch(args)
     if rank == 0 and not args.no_cpu_baseline:
-        rate, info = oracle_spmv_rate(8, k, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-                                "sample": f"CSR SpMV of the oracle's assembled matrix on {info['n']}^3 cells, k={k} ({info['dofs']} DoF), {info['reps']} SpMVs in {info['seconds']:.1f} s"}
+        base = oracle_spmv_baselines(8, k, args.cpu_seconds / 2)
+        line["cpu_baseline"] = base["all"]
+        line["cpu_baseline_1core"] = base["one"]
         if args.solve_n > 0:
             line["solve"]["cpu_baseline"] = oracle_solve_rate(4, args.solve_k)
     if rank == 0:
@@ -687,6 +753,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-n", type=int, default=96, help="mesh of the mixed-vs-FP64 solve sub-benchmark (0: skip)")
     ap.add_argument("--solve-k", type=int, default=3)
+    ap.add_argument("--solve-reps", type=int, default=3, help="timed solves per arm of the solve sub-benchmark (median reported)")
     ap.add_argument("--sweep-n", type=int, default=64, help="mesh of the FP64 apply sweep over k = 1..5 (0: skip)")
     ap.add_argument("--smooth-n", type=int, default=64, help="mesh of the smoothing-step sub-benchmark (0: skip)")
     ap.add_argument("--batch", type=int, default=64, help="batched uneven solves (0: skip)")

@@ -226,6 +226,14 @@ int stk_restrict(stk_problem* P, int fine_level, int dtype, const void* rf, void
  * allocates that dtype's multigrid workspace (three vectors per level). */
 int stk_smooth(stk_problem* P, int level, int dtype, void* x, const void* b);
 
+/* One colour of the smoothing step of Algorithm 2 (Sec. 3.1): r = b - A x
+ * for the current x, then on every patch of colour `colour` (0..7, the
+ * colour (i mod 2) + 2 (j mod 2) + 4 (l mod 2) of the patch's vertex (i, j, l))
+ * the local solve of Sec. 3.2 and x += R_j^T (U, P).  Calling it for the
+ * colours 0..7 in turn is exactly stk_smooth.  Same workspace, options and
+ * errors as stk_smooth; STK_EINVAL for a colour outside 0..7. */
+int stk_smooth_colour(stk_problem* P, int level, int dtype, int colour, void* x, const void* b);
+
 /* One smoothing step (as stk_smooth: Algorithm 2, Sec. 3.1) of `count`
  * problems of the same degree k, batched (the merged launches have no
  * counterpart in the paper, which smooths one problem): per colour, every problem's colour residual, then ONE launch of
@@ -280,7 +288,7 @@ int stk_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve
  * infos may be NULL, else count entries.  Synchronous.  Returns STK_OK,
  * STK_ENOCONV if any solve reached its max_iter, or the first other error;
  * stk_last_error(NULL) names the failing problem.  No problem may appear
- * twice. */
+ * twice and x[i] must not alias b[i] (STK_EINVAL before any launch). */
 int stk_solve_batch(stk_problem* const* problems, int count, const double* const* b, double* const* x, double rtol,
                     stk_solve_info* infos);
 
@@ -288,7 +296,9 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
  * apply in `dtype` with each candidate march length of its velocity kernel
  * (cells per CTA: n, n/2, ..., 2) on the problem's stream and keep the
  * fastest; every later apply, residual, smoothing step and solve of that dtype
- * uses it.  Synchronous; allocates and frees two vectors per level. */
+ * uses it (a V-cycle graph that an earlier solve captured in that dtype is
+ * discarded, so the next solve captures the tuned launches).  Synchronous;
+ * allocates and frees two vectors per level. */
 int stk_autotune(stk_problem* P, int dtype);
 
 /* The march length chosen by stk_autotune for a level and dtype (0 = not

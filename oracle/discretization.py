@@ -288,6 +288,70 @@ class Discretization:
         A.eliminate_zeros()
         return A
 
+    # --------------------------------------------------- rows from a cell subset
+    def local_rows(self, cells):
+        """The global matrix restricted to the DoFs of a set of cells, built
+        from the same local pieces as `assemble` without a global matrix.
+
+        Sums the cell matrices of `cells` (array (ncell, 3)), the interior-face
+        matrices of every face of those cells (whether or not the cell on the
+        other side is in the set) and the boundary-face matrices of their faces
+        on the domain boundary.  Returns (cols, K): cols the sorted global DoFs
+        these pieces touch, K a CSR matrix over cols.  A row of K equals the
+        global matrix's row (over cols) for every DoF whose cells all belong
+        to `cells`: then every cell and face contributing to that row is
+        included.  Constrained DoFs have zero rows and columns; entries below
+        1e-12 of the largest are dropped, as in `assemble`.
+        """
+        cells = np.atleast_2d(np.asarray(cells, dtype=np.int64))
+        n = self.n
+        nvl = self.n_local_velocity()
+        pieces = [(self.cell_dofs(cells), self.cell_matrix())]
+        inner = {d: set() for d in range(3)}
+        bnd = {(d, s): set() for d in range(3) for s in (0, 1)}
+        for cell in map(tuple, cells):
+            for d in range(3):
+                if cell[d] > 0:
+                    lo = list(cell)
+                    lo[d] -= 1
+                    inner[d].add(tuple(lo))
+                else:
+                    bnd[(d, 0)].add(cell)
+                if cell[d] < n - 1:
+                    inner[d].add(cell)
+                else:
+                    bnd[(d, 1)].add(cell)
+        for d in range(3):
+            if inner[d]:
+                lower = np.array(sorted(inner[d]), dtype=np.int64)
+                upper = lower.copy()
+                upper[:, d] += 1
+                Gf = np.concatenate([self.cell_dofs(lower)[:, :nvl], self.cell_dofs(upper)[:, :nvl]], axis=1)
+                pieces.append((Gf, self.interior_face_matrix(d)))
+            for s in (0, 1):
+                if bnd[(d, s)]:
+                    sel = np.array(sorted(bnd[(d, s)]), dtype=np.int64)
+                    pieces.append((self.cell_dofs(sel)[:, :nvl], self.boundary_face_matrix(d, s)))
+        cols = np.unique(np.concatenate([G.reshape(-1) for G, _ in pieces]))
+        rows_l, cols_l, vals = [], [], []
+        for G, Kloc in pieces:
+            scale = np.abs(Kloc).max()
+            ia, ib = np.nonzero(np.abs(Kloc) > 1e-15 * scale)
+            Gl = np.searchsorted(cols, G)
+            rows_l.append(Gl[:, ia].reshape(-1))
+            cols_l.append(Gl[:, ib].reshape(-1))
+            vals.append(np.broadcast_to(Kloc[ia, ib], (G.shape[0], len(ia))).reshape(-1))
+        nc = len(cols)
+        K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows_l), np.concatenate(cols_l))), shape=(nc, nc))
+        K.sum_duplicates()
+        scale = np.abs(K.data).max()
+        K.data[np.abs(K.data) < _DROP * scale] = 0.0
+        K.eliminate_zeros()
+        f = sp.diags(self.free_mask()[cols].astype(np.float64))
+        K = (f @ K @ f).tocsr()
+        K.eliminate_zeros()
+        return cols, K
+
     # ------------------------------------------------------- sampled row products
     def apply_rows(self, x: np.ndarray, rows: np.ndarray) -> np.ndarray:
         """(A x)[rows] from the local matrices, without a global matrix.

@@ -89,6 +89,7 @@ def load_library():
         "stk_solve": (ctypes.c_int, [P, P, P, ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_rhs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P]),
         "stk_smooth_static": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P]),
+        "stk_smooth_colour": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
         "stk_autotune": (ctypes.c_int, [P, ctypes.c_int]),
         "stk_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
@@ -284,6 +285,13 @@ class StokesMG:
         level = self._lvl(level)
         dt = self._dt(x)
         self._check(self.lib.stk_smooth(self.h, level, dt, self._vec(x, level), self._vec(b, level, dt)))
+        return x
+
+    def smooth_colour(self, colour: int, x, b, level: int = -1):
+        """One colour of Algorithm 2 on `level` (residual, then that colour's patch solves), x in place."""
+        level = self._lvl(level)
+        dt = self._dt(x)
+        self._check(self.lib.stk_smooth_colour(self.h, level, dt, int(colour), self._vec(x, level), self._vec(b, level, dt)))
         return x
 
     def smooth_static(self, x, b, level: int = -1):

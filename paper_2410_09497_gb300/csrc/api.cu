@@ -341,6 +341,15 @@ int stk_smooth(stk_problem* P, int level, int dtype, void* x, const void* b) {
   return status_of(P, stk::run_smooth(P, level, dtype, x, b), "smooth");
 }
 
+int stk_smooth_colour(stk_problem* P, int level, int dtype, int colour, void* x, const void* b) {
+  int rc = check_level(P, level);
+  if (rc) return rc;
+  if ((rc = check_dtype(P, dtype)) || (rc = check_vec(P, x, "x")) || (rc = check_vec(P, b, "b"))) return rc;
+  if (colour < 0 || colour > 7) return fail(P, STK_EINVAL, "colour must be in 0..7");
+  if (x == b) return fail(P, STK_EINVAL, "x and b must not alias");
+  return status_of(P, stk::run_smooth_colour(P, level, dtype, colour, x, b), "smooth_colour");
+}
+
 int stk_smooth_batch(stk_problem* const* problems, int count, const int* levels, int dtype, void* const* x,
                      const void* const* b) {
   if (!problems || count < 1 || !levels || !x || !b) return fail(nullptr, STK_EINVAL, "smooth_batch: empty or NULL arguments");
@@ -401,6 +410,8 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
   for (int i = 0; i < count; ++i) {
     stk_problem* P = problems[i];
     if (!P) return fail(nullptr, STK_EINVAL, "solve_batch: NULL problem");
+    // an in-place call would zero b with x at the start of the solve
+    if ((const void*)x[i] == (const void*)b[i]) return fail(nullptr, STK_EINVAL, "solve_batch: x and b must not alias");
     int rc;
     if ((rc = check_mg(P)) || (rc = check_vec(P, b[i], "b")) || (rc = check_vec(P, x[i], "x"))) {
       g_setup_error = "problem " + std::to_string(i) + ": " + P->err;
@@ -450,6 +461,15 @@ int stk_autotune(stk_problem* P, int dtype) {
     if (x) cudaFree(x);
     if (y) cudaFree(y);
   }
+  // a V-cycle graph captured before tuning replays the old launch shapes:
+  // drop it so that the next solve captures the tuned ones
+  stk::MgWork& W = P->mg[dtype];
+  if (W.graph) {
+    cudaStreamSynchronize(P->stream);
+    cudaGraphExecDestroy(W.graph);
+  }
+  W.graph = nullptr;
+  W.vcycle_runs = 0;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return status_of(P, e, "autotune");

@@ -246,6 +246,7 @@ cudaError_t coarse3_solve(stk_problem* P);
 cudaError_t ensure_mg_workspace(stk_problem* P, int dtype);
 cudaError_t ensure_coarse(stk_problem* P);
 cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void* b);
+cudaError_t run_smooth_colour(stk_problem* P, int level, int dtype, int colour, void* x, const void* b);
 cudaError_t run_smooth_batch(stk_problem* const* Ps, const int* levels, int count, int dtype, void* const* x,
                              const void* const* b);
 cudaError_t run_vcycle(stk_problem* P, int dtype, const void* b, void* x);

@@ -219,6 +219,17 @@ cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void
   return cudaSuccess;
 }
 
+// One colour of Algorithm 2: r = b - A x, then the colour's patch solves.
+cudaError_t run_smooth_colour(stk_problem* P, int level, int dtype, int colour, void* x, const void* b) {
+  cudaError_t e = ensure_mg_workspace(P, dtype);
+  if (e == cudaSuccess && P->opt.local_cg_mode == STK_LOCAL_DIRECT) e = ensure_direct(P, level);
+  if (e != cudaSuccess) return e;
+  void* r = P->mg[dtype].r[level];
+  e = launch_apply(P, level, dtype, x, b, r, -1.0);
+  if (e == cudaSuccess) e = launch_patch_colour(P, level, dtype, colour, r, x);
+  return e;
+}
+
 // One smoothing step of several problems of the same degree, all on the first
 // problem's stream: per colour, every problem's colour residual, then one
 // patch launch over the colour's patches of all of them.

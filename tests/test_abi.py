@@ -52,6 +52,14 @@ def test_invalid_arguments_fail_without_gpu(lib):
     assert lib.stk_smooth_batch(None, 0, None, 0, None, None) == -1
     assert b"smooth_batch" in lib.stk_last_error(None)
     assert lib.stk_solve_batch(None, 0, None, None, ctypes.c_double(1e-8), None) == -1
+    # an in-place batched solve (x[i] == b[i]) is refused before the problem is
+    # touched (the handle here is a host buffer that no call may use)
+    dummy = ctypes.create_string_buffer(256)
+    probs = (ctypes.c_void_p * 1)(ctypes.addressof(dummy))
+    same = (ctypes.c_void_p * 1)(4096)
+    lib.stk_solve_batch.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+    assert lib.stk_solve_batch(probs, 1, same, same, ctypes.c_double(1e-8), None) == -1
+    assert b"alias" in lib.stk_last_error(None)
 
 
 def test_binding_layout_matches_oracle_numbering():

@@ -15,6 +15,8 @@ from oracle.multigrid import Hierarchy
 from oracle.transfer import prolongation
 from seeded_inputs import manufactured_coefficients, random_vector
 
+from _parity import check
+
 pytestmark = pytest.mark.gpu
 
 
@@ -41,19 +43,19 @@ def test_transfers(stk, k, nf):
     xf0 = random_vector(400 + k, F.N) * F.free_mask()
     out = dev(xf0.copy())
     P.prolongate_add(dev(xc), out)
-    assert relerr(out.cpu().numpy(), xf0 + Pm @ xc) <= 1e-12
+    check(relerr(out.cpu().numpy(), xf0 + Pm @ xc), 1e-12)
     rf = random_vector(500 + k, F.N)
     rc = torch.full((C.N,), float("nan"), dtype=torch.float64, device="cuda")
     P.restrict(dev(rf), rc)
-    assert relerr(rc.cpu().numpy(), Pm.T @ (rf * F.free_mask())) <= 1e-12
+    check(relerr(rc.cpu().numpy(), Pm.T @ (rf * F.free_mask())), 1e-12)
     # FP32
     out32 = dev(xf0.astype(np.float32))
     P.prolongate_add(dev(xc.astype(np.float32)), out32)
     ref = xf0.astype(np.float32).astype(float) + Pm @ xc.astype(np.float32).astype(float)
-    assert relerr(out32.cpu().numpy().astype(float), ref) <= 1e-5
+    check(relerr(out32.cpu().numpy().astype(float), ref), 1e-5)
     rc32 = torch.empty(C.N, dtype=torch.float32, device="cuda")
     P.restrict(dev(rf.astype(np.float32)), rc32)
-    assert relerr(rc32.cpu().numpy().astype(float), Pm.T @ (rf.astype(np.float32).astype(float) * F.free_mask())) <= 1e-5
+    check(relerr(rc32.cpu().numpy().astype(float), Pm.T @ (rf.astype(np.float32).astype(float) * F.free_mask())), 1e-5)
     P.close()
 
 
@@ -67,11 +69,11 @@ def test_smooth_fixed_cg_matches_oracle(stk, n, k, iters):
     P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=iters)
     x = dev(x0.copy())
     P.smooth(x, dev(b))
-    assert relerr(x.cpu().numpy(), ref) <= 1e-11
+    check(relerr(x.cpu().numpy(), ref), 1e-11)
     # FP32 smoother against the same FP64 reference
     x32 = dev(x0.astype(np.float32))
     P.smooth(x32, dev(b.astype(np.float32)))
-    assert relerr(x32.cpu().numpy().astype(float), ref) <= 2e-4
+    check(relerr(x32.cpu().numpy().astype(float), ref), 2e-4)
     P.close()
 
 
@@ -85,7 +87,7 @@ def test_smooth_converged_cg_equals_direct(stk, n, k):
     P = stk.StokesMG(n, k, local_cg_mode=stk.CG_TOL, local_cg_iters=2000, local_cg_tol=1e-14)
     x = dev(x0.copy())
     P.smooth(x, dev(b))
-    assert relerr(x.cpu().numpy(), ref) <= 1e-10
+    check(relerr(x.cpu().numpy(), ref), 1e-10)
     P.close()
 
 
@@ -100,7 +102,7 @@ def test_coarse_solve_is_pseudo_inverse(stk, k):
     P.coarse_solve(dev(b), x)
     xs = x.cpu().numpy()
     # both are mean-free in the pressure coefficients; compare directly
-    assert relerr(xs, ref) <= 1e-10
+    check(relerr(xs, ref), 1e-10)
     P.close()
 
 
@@ -113,10 +115,10 @@ def test_vcycle_matches_oracle(stk, n, k):
     P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
     x = dev(np.full(d.N, np.nan))
     P.vcycle(dev(b), x)
-    assert relerr(x.cpu().numpy(), ref) <= 1e-10
+    check(relerr(x.cpu().numpy(), ref), 1e-10)
     x32 = dev(np.full(d.N, np.nan, dtype=np.float32))
     P.vcycle(dev(b.astype(np.float32)), x32)
-    assert relerr(x32.cpu().numpy().astype(float), ref) <= 5e-4
+    check(relerr(x32.cpu().numpy().astype(float), ref), 5e-4)
     P.close()
 
 
@@ -137,10 +139,10 @@ def test_solve_matches_oracle(stk, n, k):
         assert info["converged"] and true_rel <= 1e-8
         if prec == stk.PREC_FP64:
             assert info["iterations"] == info_ref["iterations"]
-            assert relerr(xs, ref) <= 1e-9
+            check(relerr(xs, ref), 1e-9)
         else:
             assert abs(info["iterations"] - info_ref["iterations"]) <= 1
-            assert relerr(xs, ref) <= 1e-6
+            check(relerr(xs, ref), 1e-6)
         P.close()
 
 
@@ -154,7 +156,7 @@ def test_rhs_matches_oracle(stk, n, k, nu):
     P = stk.StokesMG(n, k, nu)
     b = torch.full((d.N,), float("nan"), dtype=torch.float64, device="cuda")
     P.rhs(coef, b)
-    assert relerr(b.cpu().numpy(), ref) <= 1e-12
+    check(relerr(b.cpu().numpy(), ref), 1e-12)
     P.close()
 
 
@@ -169,13 +171,13 @@ def test_coarse_solve_on_3cube(stk, k):
     P = stk.StokesMG(3, k)
     x = dev(np.full(d.N, np.nan))
     P.coarse_solve(dev(b), x)
-    assert relerr(x.cpu().numpy(), ref) <= 1e-10
+    check(relerr(x.cpu().numpy(), ref), 1e-10)
     # consistent right-hand side, FP32 in and out (the solve itself runs in FP64)
     b[d.offsets[3]:] -= b[d.offsets[3]:].mean()
     ref = H.coarse_solve(b)
     x32 = dev(np.full(d.N, np.nan, dtype=np.float32))
     P.coarse_solve(dev(b.astype(np.float32)), x32)
-    assert relerr(x32.cpu().numpy().astype(np.float64), ref) <= 1e-5
+    check(relerr(x32.cpu().numpy().astype(np.float64), ref), 1e-5)
     P.close()
 
 
@@ -196,7 +198,7 @@ def test_coarse_factors_shared_and_keyed(stk):
             P.coarse_solve(dev(b), x)
             xs.append(x.cpu().numpy())
         assert np.array_equal(xs[0], xs[1])  # same factors, same kernels
-        assert relerr(xs[0], ref) <= 1e-10
+        check(relerr(xs[0], ref), 1e-10)
         results[(nu, pf)] = xs[0]
         for P in Ps:
             P.close()
@@ -213,7 +215,7 @@ def test_vcycle_and_solve_on_3cube_hierarchy(stk, n, k):
     P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
     x = dev(np.full(d.N, np.nan))
     P.vcycle(dev(b), x)
-    assert relerr(x.cpu().numpy(), ref) <= 1e-10
+    check(relerr(x.cpu().numpy(), ref), 1e-10)
     xs = dev(np.zeros(d.N))
     info = P.solve(dev(b), xs, rtol=1e-8)
     _, info_ref = H.solve(b, tol=1e-8)
@@ -281,10 +283,10 @@ def test_smooth_direct_equals_oracle_lu(stk, n, k):
     P = stk.StokesMG(n, k, local_cg_mode=stk.LOCAL_DIRECT)
     x = dev(x0.copy())
     P.smooth(x, dev(b))
-    assert relerr(x.cpu().numpy(), ref) <= 1e-10
+    check(relerr(x.cpu().numpy(), ref), 1e-10)
     x32 = dev(x0.astype(np.float32))
     P.smooth(x32, dev(b.astype(np.float32)))
-    assert relerr(x32.cpu().numpy().astype(float), ref) <= 2e-4
+    check(relerr(x32.cpu().numpy().astype(float), ref), 2e-4)
     P.close()
 
 

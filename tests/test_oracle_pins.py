@@ -247,6 +247,27 @@ def test_apply_rows_matches_assembly():
     assert np.abs(d.apply_rows(x, rows) - (A @ x)[rows]).max() < 1e-13 * np.abs(A @ x).max()
 
 
+@pytest.mark.parametrize("n,k,vertex", [(4, 2, (2, 2, 2)), (4, 2, (1, 2, 3)), (5, 1, (4, 1, 2)), (4, 3, (3, 3, 1))])
+def test_local_rows_of_a_patch_match_assembly(n, k, vertex):
+    """The rows of the patch DoFs built from the patch's eight cells and their
+    faces alone equal those rows of the globally assembled matrix, for an
+    interior patch and for patches touching the boundary: the route the
+    full-size smoother checks take, pinned against the global assembly."""
+    d = Discretization(n, k)
+    A = d.assemble()
+    J = patch_dofs(d, vertex)
+    cells = [(vertex[0] - 1 + a, vertex[1] - 1 + b, vertex[2] - 1 + c) for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+    cols, K = d.local_rows(cells)
+    pos = np.searchsorted(cols, J)
+    assert np.array_equal(cols[pos], J)
+    ref = A[J][:, cols].toarray()
+    got = K[pos].toarray()
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
+    # and nothing outside cols couples to the patch rows
+    outside = np.setdiff1d(np.arange(d.N), cols)
+    assert A[J][:, outside].nnz == 0
+
+
 # ---------------------------------------------------- manufactured solution
 def test_manufactured_solution_properties():
     man = Manufactured(manufactured_coefficients(0), nu=1.3)

@@ -40,6 +40,38 @@ def test_static_smoother_matches_allocating_smoother_twice(stk, n, k):
     P.close()
 
 
+def test_static_smoother_allocates_nothing_on_a_fresh_problem(stk, monkeypatch):
+    """With every library allocation made to fail (the host-side injector,
+    STK_FAIL_ALLOC_AFTER=0), stk_smooth_static still runs on a problem that no
+    other smoothing call has touched (no workspace exists yet), twice in a row,
+    and matches stk_smooth run afterwards on a second problem built the same way."""
+    import torch
+
+    n, k = 4, 3
+    d = Discretization(n, k)
+    x0 = random_vector(2300, d.N) * d.free_mask()
+    b = torch.from_numpy(random_vector(2301, d.N) * d.free_mask()).cuda()
+    fresh = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
+    xs = torch.from_numpy(x0).cuda()
+    monkeypatch.setenv("STK_FAIL_ALLOC_AFTER", "0")
+    fresh.smooth_static(xs, b)
+    fresh.smooth_static(xs, b)
+    torch.cuda.synchronize()
+    # the injector is live: an allocating call on the same problem fails
+    with pytest.raises(stk.StokesError) as err:
+        fresh.smooth(xs.clone(), b)
+    assert err.value.code == -3
+    monkeypatch.delenv("STK_FAIL_ALLOC_AFTER")
+    other = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
+    xa = torch.from_numpy(x0).cuda()
+    other.smooth(xa, b)
+    other.smooth(xa, b)
+    torch.cuda.synchronize()
+    assert _relerr(xs.cpu().numpy(), xa.cpu().numpy()) <= 1e-12
+    fresh.close()
+    other.close()
+
+
 def test_static_smoother_rejects_levels_beyond_its_array(stk):
     import torch
 
