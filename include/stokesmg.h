@@ -80,6 +80,11 @@ typedef struct stk_options {
   void* stream;          /* cudaStream_t used by every call, NULL = default stream     */
   int use_graphs;        /* 1 (default): stk_solve replays its V-cycle as a captured
                             CUDA graph (needs a non-NULL stream); 0: direct launches */
+  int fused_smoother;    /* 1 (default): each colour of the smoother computes its patch
+                            residuals inside the patch kernel from the current x and b
+                            (every coupling across the patch boundary kept); 0: one
+                            residual apply of the whole level per colour first, then
+                            the patch kernel.  Same result up to rounding. */
 } stk_options;
 
 typedef struct stk_problem stk_problem;

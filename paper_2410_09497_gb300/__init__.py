@@ -39,6 +39,7 @@ class Options(ctypes.Structure):
         ("penalty_factor", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("use_graphs", ctypes.c_int),
+        ("fused_smoother", ctypes.c_int),
     ]
 
 
@@ -177,7 +178,8 @@ class StokesMG:
 
     def __init__(self, n: int, k: int, nu: float = 1.0, *, precision: int = PREC_FP64, gmres_restart: int = 20,
                  max_iter: int = 200, local_cg_mode: int = CG_FIXED, local_cg_iters: int = 15,
-                 local_cg_tol: float = 1e-8, penalty_factor: float = 1.0, use_graphs: bool = True, stream=None):
+                 local_cg_tol: float = 1e-8, penalty_factor: float = 1.0, use_graphs: bool = True,
+                 fused_smoother: bool = True, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -190,6 +192,7 @@ class StokesMG:
         opt.local_cg_mode, opt.local_cg_iters, opt.local_cg_tol = local_cg_mode, local_cg_iters, local_cg_tol
         opt.penalty_factor = penalty_factor
         opt.use_graphs = 1 if use_graphs else 0
+        opt.fused_smoother = 1 if fused_smoother else 0
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         opt.stream = ctypes.c_void_p(s.cuda_stream)

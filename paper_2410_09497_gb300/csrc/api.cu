@@ -110,6 +110,7 @@ int stk_default_options(stk_options* opt) {
   opt->penalty_factor = 1.0;
   opt->stream = nullptr;
   opt->use_graphs = 1;
+  opt->fused_smoother = 1;
   return STK_OK;
 }
 
@@ -216,6 +217,8 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
     stk::fill_cell_tables(L.t1d, &h32);
     L.htab64 = h64;
     L.htab32 = h32;
+    stk::fill_contract_tables(L.t1d, &L.hce64);
+    stk::fill_contract_tables(L.t1d, &L.hce32);
     const stk::PatchTables1D pt = stk::build_patch_tables(L.t1d);
     L.eo_interior = pt.eo_c && pt.eo_d[0];
     stk::PatchTables<double> p64;

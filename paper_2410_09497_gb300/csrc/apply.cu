@@ -15,7 +15,10 @@
 // along the continuous direction c through a chunk of cells.  Per cell it
 // stages the k+1 new node layers of u_c (plus one cell of halo in d1 and d2)
 // in shared memory, forms t = M_d2 L_d1 u + M_d1 L_d2 u per node, and then
-// contracts along c in registers with the cell matrices KC, MC and D^T.  The
+// contracts along c in registers with the cell matrices KC, MC and D^T, in
+// even-odd form: KC and MC are centro-symmetric and D antisymmetric under the
+// reflection of the cell, so the contraction works on sums and differences of
+// mirrored nodes with half the products (ContractTables).  The
 // contribution of a cell to its upper shared node is carried to the next step,
 // so no face or node is computed twice inside a chunk; a chunk re-does only
 // the cell below it.  Pressure kernel: one thread per pressure node.
@@ -28,10 +31,11 @@ namespace stk {
 template <typename T>
 struct ApplyArgs {
   const T* x;
-  const T* b;  // optional: y = alpha A x + b
+  const T* b;  // residual form: y = b - A x; NULL: y = A x
   T* y;
-  T alpha;
-  CellTables<T> tv;  // by value: constant-bank operands for compile-time indices
+  T alpha;     // -1 in the residual form, 1 otherwise (pressure kernel)
+  CellTables<T> tv;      // by value: constant-bank operands for compile-time indices
+  ContractTables<T> ce;  // even-odd contraction along c, by value
   int n, m;
   int chunk, nchunks, ntile;
 };
@@ -169,7 +173,7 @@ __device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, cons
 // CTA per SM (the register count the compiler picks unbounded) left the FP64
 // pipe half idle at k = 4 and 5; the register cap costs a few spills there and
 // measured 1.2-1.3x faster at 64^3.
-template <int K, typename T>
+template <int K, typename T, bool RES>
 __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_velocity_kernel(ApplyArgs<T> A) {
   using Cfg = ApplyCfg<K>;
   constexpr int ND = Cfg::ND, NC = Cfg::NC, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
   const T* u = A.x + c * nvel;
   const T* p = A.x + 3 * nvel;
   T* yc = A.y + c * nvel;
-  const T* bc = A.b ? A.b + c * nvel : nullptr;
+  const T* bc = RES ? A.b + c * nvel : nullptr;
 
   for (int i = tid; i < (int)(sizeof(CellTables<T>) / sizeof(T)); i += NT)
     reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(&A.tv)[i];
@@ -248,7 +252,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
       pv_next[q] = p[(int64_t)(cstart * ND + q) * psc + pline_off];
-      b_next[q] = bc ? bc[(int64_t)(cstart * ND + q) * sc + line_off] : T(0);
+      b_next[q] = RES ? bc[(int64_t)(cstart * ND + q) * sc + line_off] : T(0);
     }
   }
   __syncthreads();
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
 #pragma unroll
         for (int q = 0; q < ND; ++q) {
           pv_next[q] = p[(int64_t)((cc + 1) * ND + q) * psc + pline_off];
-          b_next[q] = bc ? bc[(int64_t)((cc + 1) * ND + q) * sc + line_off] : T(0);
+          b_next[q] = RES ? bc[(int64_t)((cc + 1) * ND + q) * sc + line_off] : T(0);
         }
       }
     }
@@ -298,14 +302,45 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
         tv[a] = sl * acc1 + sj * acc2;
         uv[a] = ss * U[(a * J + tl + H) * J + tj + H];
       }
+      // contraction along c, even-odd form (ContractTables)
+      constexpr int P = NC / 2, Q = ND / 2;
+      constexpr bool CC = NC % 2 == 1, CD = ND % 2 == 1;
+      constexpr int NE = P + (CC ? 1 : 0), QE = Q + (CD ? 1 : 0);
+      T ue[NE], te[NE], uo[P], to[P], pe[QE], po[Q];
 #pragma unroll
-      for (int i = 0; i < NC; ++i) {
-        T acc = T(0);
+      for (int a = 0; a < P; ++a) {
+        ue[a] = uv[a] + uv[NC - 1 - a];
+        uo[a] = uv[a] - uv[NC - 1 - a];
+        te[a] = tv[a] + tv[NC - 1 - a];
+        to[a] = tv[a] - tv[NC - 1 - a];
+      }
+      if constexpr (CC) {
+        ue[P] = uv[P];
+        te[P] = tv[P];
+      }
 #pragma unroll
-        for (int a = 0; a < NC; ++a) acc += A.tv.KC[i * NC + a] * uv[a] + A.tv.MC[i * NC + a] * tv[a];
+      for (int q = 0; q < Q; ++q) {
+        pe[q] = pv[q] + pv[ND - 1 - q];
+        po[q] = pv[q] - pv[ND - 1 - q];
+      }
+      if constexpr (CD) pe[Q] = pv[Q];
 #pragma unroll
-        for (int q = 0; q < ND; ++q) acc += A.tv.D[q * NC + i] * pv[q];
-        z[i] = acc;
+      for (int i = 0; i < NE; ++i) {
+        T ze = T(0), zo = T(0);
+#pragma unroll
+        for (int a = 0; a < NE; ++a) ze += A.ce.EK[i * kMaxC + a] * ue[a] + A.ce.EM[i * kMaxC + a] * te[a];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) ze += A.ce.ED[i * kMaxD + q] * po[q];
+        if (i < P) {
+#pragma unroll
+          for (int a = 0; a < P; ++a) zo += A.ce.OK[i * kMaxC + a] * uo[a] + A.ce.OM[i * kMaxC + a] * to[a];
+#pragma unroll
+          for (int q = 0; q < QE; ++q) zo += A.ce.OD[i * kMaxD + q] * pe[q];
+          z[i] = ze + zo;
+          z[NC - 1 - i] = ze - zo;
+        } else {
+          z[i] = ze;
+        }
       }
       if (!warm) {
 #pragma unroll
@@ -313,7 +348,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
           const int ic = cc * ND + i;
           const int64_t g = (int64_t)ic * sc + line_off;
           T val = (i == 0) ? z[0] + zcar : z[i];
-          val = A.alpha * val + bv[i];
+          if constexpr (RES) val = bv[i] - val;
           yc[g] = (ic == 0) ? T(0) : val;
         }
         if (cc == n - 1) yc[(int64_t)m * sc + line_off] = T(0);
@@ -370,8 +405,10 @@ __global__ void __launch_bounds__(256) apply_pressure_kernel(ApplyArgs<T> A) {
 }
 
 template <int K, typename T>
-static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, const T* x, const T* b, T* y, T alpha,
-                                  int stages, cudaStream_t s) {
+static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, const ContractTables<T>& ce, const T* x,
+                                  const T* b, T* y, T alpha, int stages, cudaStream_t s) {
+  // the two forms the library uses: y = A x and y = b - A x
+  if (b ? alpha != T(-1) : alpha != T(1)) return cudaErrorInvalidValue;
   using Cfg = ApplyCfg<K>;
   ApplyArgs<T> a;
   a.x = x;
@@ -379,6 +416,7 @@ static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, cons
   a.y = y;
   a.alpha = alpha;
   a.tv = tab;
+  a.ce = ce;
   a.n = L.n;
   a.m = L.m;
   a.ntile = (L.m + Cfg::TJ - 1) / Cfg::TJ;
@@ -392,12 +430,18 @@ static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, cons
   a.nchunks = (L.n + a.chunk - 1) / a.chunk;
   dim3 grid(tiles * a.nchunks, 3);
   const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
-  static std::atomic<unsigned long long> smem_set{0};
-  {
-    const cudaError_t e = allow_dynamic_smem(apply_velocity_kernel<K, T>, smem, smem_set);
-    if (e != cudaSuccess) return e;
+  static std::atomic<unsigned long long> smem_set{0}, smem_set_res{0};
+  if (stages & 1) {
+    if (b) {
+      const cudaError_t e = allow_dynamic_smem(apply_velocity_kernel<K, T, true>, smem, smem_set_res);
+      if (e != cudaSuccess) return e;
+      apply_velocity_kernel<K, T, true><<<grid, Cfg::NT, smem, s>>>(a);
+    } else {
+      const cudaError_t e = allow_dynamic_smem(apply_velocity_kernel<K, T, false>, smem, smem_set);
+      if (e != cudaSuccess) return e;
+      apply_velocity_kernel<K, T, false><<<grid, Cfg::NT, smem, s>>>(a);
+    }
   }
-  if (stages & 1) apply_velocity_kernel<K, T><<<grid, Cfg::NT, smem, s>>>(a);
   if (stages & 2) {
     const int64_t np = (int64_t)L.m * L.m * L.m;
     int blocks = (int)std::min<int64_t>((np + 255) / 256, 152 * 16);
@@ -407,14 +451,14 @@ static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, cons
 }
 
 template <typename T>
-static cudaError_t dispatch_apply(int k, const Level& L, const CellTables<T>& tab, const T* x, const T* b, T* y,
-                                  T alpha, int stages, cudaStream_t s) {
+static cudaError_t dispatch_apply(int k, const Level& L, const CellTables<T>& tab, const ContractTables<T>& ce,
+                                  const T* x, const T* b, T* y, T alpha, int stages, cudaStream_t s) {
   switch (k) {
-    case 1: return launch_apply_k<1, T>(L, tab, x, b, y, alpha, stages, s);
-    case 2: return launch_apply_k<2, T>(L, tab, x, b, y, alpha, stages, s);
-    case 3: return launch_apply_k<3, T>(L, tab, x, b, y, alpha, stages, s);
-    case 4: return launch_apply_k<4, T>(L, tab, x, b, y, alpha, stages, s);
-    case 5: return launch_apply_k<5, T>(L, tab, x, b, y, alpha, stages, s);
+    case 1: return launch_apply_k<1, T>(L, tab, ce, x, b, y, alpha, stages, s);
+    case 2: return launch_apply_k<2, T>(L, tab, ce, x, b, y, alpha, stages, s);
+    case 3: return launch_apply_k<3, T>(L, tab, ce, x, b, y, alpha, stages, s);
+    case 4: return launch_apply_k<4, T>(L, tab, ce, x, b, y, alpha, stages, s);
+    case 5: return launch_apply_k<5, T>(L, tab, ce, x, b, y, alpha, stages, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -423,10 +467,10 @@ cudaError_t launch_apply_on(const stk_problem* P, int level, int dtype, const vo
                             double alpha, int stages, cudaStream_t stream) {
   const Level& L = P->levels[level];
   if (dtype == STK_F64)
-    return dispatch_apply<double>(P->k, L, L.htab64, (const double*)x, (const double*)b, (double*)y, alpha, stages,
-                                  stream);
-  return dispatch_apply<float>(P->k, L, L.htab32, (const float*)x, (const float*)b, (float*)y, (float)alpha, stages,
-                               stream);
+    return dispatch_apply<double>(P->k, L, L.htab64, L.hce64, (const double*)x, (const double*)b, (double*)y, alpha,
+                                  stages, stream);
+  return dispatch_apply<float>(P->k, L, L.htab32, L.hce32, (const float*)x, (const float*)b, (float*)y, (float)alpha,
+                               stages, stream);
 }
 
 cudaError_t launch_apply(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,

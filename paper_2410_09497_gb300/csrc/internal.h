@@ -72,6 +72,28 @@ struct CellTables {
   T S[kMaxD];
 };
 
+// The contraction along the continuous direction in even-odd form.  KC and
+// MC are centro-symmetric and D is antisymmetric under the reflection of a
+// cell (its Gauss-Lobatto and Gauss nodes are symmetric), so with the
+// P = (k+2)/2 node pairs (a, k+1-a) of the continuous basis, sums
+// ue[a] = u[a] + u[k+1-a] (and the centre node when k+2 is odd) and
+// differences uo[a] = u[a] - u[k+1-a], and the same for the Q = (k+1)/2
+// pressure pairs, the half-sums and half-differences of the outputs are
+//   Ze[i] = sum_a EK[i][a] ue[a] + EM[i][a] te[a] + sum_q ED[i][q] po[q]
+//   Zo[i] = sum_a OK[i][a] uo[a] + OM[i][a] to[a] + sum_q OD[i][q] pe[q]
+// and z[i] = Ze[i] + Zo[i], z[k+1-i] = Ze[i] - Zo[i] (the centre output is
+// Ze[P]): about half the products of the dense form.  Row-major with row
+// length kMaxC (EK, EM, OK, OM) or kMaxD (ED, OD).
+template <typename T>
+struct ContractTables {
+  T EK[kMaxC * kMaxC];
+  T EM[kMaxC * kMaxC];
+  T OK[kMaxC * kMaxC];
+  T OM[kMaxC * kMaxC];
+  T ED[kMaxC * kMaxD];
+  T OD[kMaxC * kMaxD];
+};
+
 // Host-side double precision 1D data of one (k, h, nu, penalty) combination.
 struct Tables1D {
   int k = 0;
@@ -146,6 +168,8 @@ Tables1D build_tables(int k, double h, double nu, double penalty_factor);
 
 template <typename T>
 void fill_cell_tables(const Tables1D& t, CellTables<T>* out);
+template <typename T>
+void fill_contract_tables(const Tables1D& t, ContractTables<T>* out);
 
 struct Level {
   int n = 0, m = 0;
@@ -156,6 +180,8 @@ struct Level {
   CellTables<float>* tab32 = nullptr;   // device
   CellTables<double> htab64{};          // host copies, passed to kernels by value
   CellTables<float> htab32{};
+  ContractTables<double> hce64{};       // even-odd contraction tables, by value
+  ContractTables<float> hce32{};
   int apply_chunk[2] = {0, 0};          // cells per CTA march of the apply ([dtype]); 0 = default
   PatchTables<double>* ptab64 = nullptr;  // device
   PatchTables<float>* ptab32 = nullptr;   // device
@@ -222,6 +248,12 @@ cudaError_t launch_restrict(const stk_problem* P, int fine_level, int dtype, con
 // smoother.cu
 int patch_local_size(int k);
 cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x);
+// the fused colour (patch residual computed in the kernel): xout = xin + the
+// colour's corrections at its patch DoFs; xin and xout must not alias
+cudaError_t launch_patch_colour_fused(const stk_problem* P, int level, int dtype, int colour, const void* xin,
+                                      const void* b, void* xout);
+// xout = xin at every entry no patch of the colour owns
+cudaError_t launch_copy_unowned(const stk_problem* P, int level, int dtype, int colour, const void* xin, void* xout);
 cudaError_t launch_patch_colour_cg(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x,
                                    int cg_tol_mode, int cg_iters, double cg_tol);
 cudaError_t launch_coarse_columns(const stk_problem* P, double* cols, int max_iter, double tol);

@@ -64,7 +64,10 @@ struct PatchOcc {
 template <typename T>
 struct PatchArgs {
   const T* r;     // colour residual (mode 0)
-  T* x;           // solution, updated in place (mode 0)
+  T* x;           // solution, updated in place (mode 0); the output x_out (mode 3)
+  const T* xin;   // mode 3: the solution before the colour (x_in), read only
+  const T* b;     // mode 3: right-hand side
+  const CellTables<T>* ctab;  // mode 3: the level's 1D cell matrices
   double* cols;   // mode 1: column-major output, N_p x N_p
   const PatchTables<T>* tab;
   int n, m;
@@ -72,7 +75,8 @@ struct PatchArgs {
   int cnt[3];     // patches of the colour per direction
   int part;       // mode 0: 0 every patch, 1 interior patches only, 2 boundary patches only
   int tlo[3], cint[3];  // the interior patches: t in [tlo, tlo + cint) per direction
-  int mode;       // 0: smoother colour, 1: coarse pseudo-inverse columns, 2: Schur complement columns
+  int mode;       // 0: smoother colour, 1: coarse pseudo-inverse columns, 2: Schur complement columns,
+                  // 3: smoother colour with the patch residual computed in the kernel (fused)
   const T* const* dir;  // mode 0: (S + a 1 1^T)^{-1} per patch type t0 + 4 t1 + 16 t2 (NULL: CG)
   int btype[3];   // mode 2: the patch type in each direction
   int cg_iters;   // FIXED: exact count; TOL: limit
@@ -505,9 +509,163 @@ __device__ __forceinline__ int64_t patch_global(int j, const int* v, int m) {
   return patch_node_global<K>(c, i0, i1, i2, v, m);
 }
 
+// Index in a padded patch box of the node with coordinate ac along direction
+// c and a1, a2 along the two other directions d1 < d2.
+template <int K>
+__device__ __forceinline__ int box_index(int c, int ac, int a1, int a2) {
+  using C = PatchCfg<K>;
+  const int x = c == 0 ? ac : a1, y = c == 0 ? a1 : (c == 1 ? ac : a2), z = c == 2 ? ac : a2;
+  return x + C::BX * (y + C::NPD * z);
+}
+
+// The patch's local residual R_j (b - A x_in) computed inside the patch
+// kernel (mode 3, the fused colour step): the operator of Algorithm 1 in the
+// Kronecker form of apply.cu, evaluated at the patch DoFs only, from x_in on
+// a window of the patch's cells plus one cell of halo in the two
+// discontinuous directions of each velocity component (the face terms of
+// eq. `bilinear` couple a patch cell to its neighbour there; the continuous
+// direction needs only the patch's own 2k+3 nodes, whose two end nodes are
+// the patch-boundary normals, in x but not in the patch space).  This keeps
+// every coupling across the patch boundary: the result equals the rows R_j
+// of the global residual, which all patches of the colour read from the same
+// x_in (the kernel writes to a separate x_out).
+//   F (3 boxes): velocity rows of the patch (the gather's layout)
+//   G (1 box):   pressure rows
+//   Wn (4 boxes): window of one component, Pst (1 box): p on the patch
+//   Tb (1 box): t = M_d2 L_d1 u + M_d1 L_d2 u on the patch cross-section
+template <int K, typename T>
+__device__ __forceinline__ void patch_residual(const PatchArgs<T>& A, const int* v, const CellTables<T>& ct, T* F,
+                                               T* G, T* Wn, T* Pst, T* Tb) {
+  using C = PatchCfg<K>;
+  constexpr int ND = K + 1, NC = K + 2, NPD = C::NPD, BX = C::BX, BOX = C::BOX, NT = C::NT;
+  constexpr int WC = 2 * K + 3;  // window nodes along c: the patch's two cells
+  constexpr int WD = 4 * ND;     // window nodes along d1, d2: patch cells and one halo cell per side
+  const int m = A.m, n = A.n, tid = threadIdx.x;
+  const int64_t nvel = (int64_t)(m + 1) * m * m, mm = (int64_t)m * m;
+  // p on the patch cells, and G = b_p
+  for (int e = tid; e < NPD * NPD * NPD; e += NT) {
+    const int q0 = e % NPD, q1 = (e / NPD) % NPD, q2 = e / (NPD * NPD);
+    const int64_t g = 3 * nvel + ((int64_t)(v[0] - 1) * ND + q0) + (int64_t)m * ((v[1] - 1) * ND + q1) +
+                      mm * ((v[2] - 1) * ND + q2);
+    const int o = q0 + BX * (q1 + NPD * q2);
+    Pst[o] = A.xin[g];
+    G[o] = A.b[g];
+  }
+  for (int c = 0; c < 3; ++c) {
+    const int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+    const int64_t E0 = (c == 0) ? m + 1 : m, E1 = (c == 1) ? m + 1 : m;
+    const int64_t sc = (c == 0) ? 1 : (c == 1 ? E0 : E0 * E1);
+    const int64_t s1 = (d1 == 0) ? 1 : E0;
+    const int64_t s2 = (d2 == 1) ? E0 : E0 * E1;
+    const T* u = A.xin + c * nvel;
+    const T* bu = A.b + c * nvel;
+    const int vc = c == 0 ? v[0] : (c == 1 ? v[1] : v[2]), vd1 = c == 0 ? v[1] : v[0], vd2 = c == 2 ? v[1] : v[2];
+    const int oc = (vc - 1) * ND, o1 = (vd1 - 2) * ND, o2 = (vd2 - 2) * ND;  // window node 0, global
+    // stage the window Wn[(i WD + ll) WD + jj] in global memory order (x
+    // fastest); corners (halo in both d1 and d2) are never read; nodes outside
+    // the domain and the constrained normal nodes (index 0 or m along c) are 0
+    for (int e = tid; e < WC * WD * WD; e += NT) {
+      int i, jj, ll;
+      if (c == 0) {
+        i = e % WC;
+        const int r = e / WC;
+        jj = r % WD;
+        ll = r / WD;
+      } else if (c == 1) {
+        jj = e % WD;
+        const int r = e / WD;
+        i = r % WC;
+        ll = r / WC;
+      } else {
+        jj = e % WD;
+        const int r = e / WD;
+        ll = r % WD;
+        i = r / WD;
+      }
+      const bool hj = jj < ND || jj >= 3 * ND, hl = ll < ND || ll >= 3 * ND;
+      if (hj && hl) continue;
+      const int gc = oc + i, g1 = o1 + jj, g2 = o2 + ll;
+      T val = T(0);
+      if (gc > 0 && gc < m && g1 >= 0 && g1 < m && g2 >= 0 && g2 < m) val = u[gc * sc + g1 * s1 + g2 * s2];
+      Wn[(i * WD + ll) * WD + jj] = val;
+    }
+    __syncthreads();
+    // t on the patch cross-section (j, l), every node i along c
+    for (int e = tid; e < WC * NPD * NPD; e += NT) {
+      const int j = e % NPD, l = (e / NPD) % NPD, i = e / (NPD * NPD);
+      const int jj = ND + j, ll = ND + l;
+      const int cj = vd1 - 1 + j / ND, bj = j % ND, cl = vd2 - 1 + l / ND, bl = l % ND;
+      const int tj = cj == 0 ? 1 : (cj == n - 1 ? 2 : 0), tl = cl == 0 ? 1 : (cl == n - 1 ? 2 : 0);
+      const T* row = Wn + (i * WD + ll) * WD;
+      T a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int q = 0; q < ND; ++q) {
+        a1 += ct.LS[tj][bj * ND + q] * row[jj - bj + q];
+        a1 += ct.LLO[bj * ND + q] * row[jj - bj - ND + q];
+        a1 += ct.LHI[bj * ND + q] * row[jj - bj + ND + q];
+      }
+#pragma unroll
+      for (int q = 0; q < ND; ++q) {
+        a2 += ct.LS[tl][bl * ND + q] * Wn[(i * WD + ll - bl + q) * WD + jj];
+        a2 += ct.LLO[bl * ND + q] * Wn[(i * WD + ll - bl - ND + q) * WD + jj];
+        a2 += ct.LHI[bl * ND + q] * Wn[(i * WD + ll - bl + ND + q) * WD + jj];
+      }
+      Tb[(i * NPD + l) * NPD + j] = ct.S[bl] * a1 + ct.S[bj] * a2;
+    }
+    __syncthreads();
+    // contraction along c over the patch's two cells: velocity rows of the
+    // 2k+1 patch-interior nodes of each line (j, l), r = b - A x_in
+    for (int e = tid; e < NPD * NPD; e += NT) {
+      const int j = e % NPD, l = e / NPD;
+      const T ss = ct.S[j % ND] * ct.S[l % ND];
+      T y[WC];
+#pragma unroll
+      for (int i = 0; i < WC; ++i) y[i] = T(0);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        T uv[NC], tv[NC], pv[ND];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          uv[a] = ss * Wn[((h * ND + a) * WD + ND + l) * WD + ND + j];
+          tv[a] = Tb[((h * ND + a) * NPD + l) * NPD + j];
+        }
+#pragma unroll
+        for (int q = 0; q < ND; ++q) pv[q] = ss * Pst[box_index<K>(c, h * ND + q, j, l)];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          T z = T(0);
+#pragma unroll
+          for (int bb = 0; bb < NC; ++bb) z += ct.KC[a * NC + bb] * uv[bb] + ct.MC[a * NC + bb] * tv[bb];
+#pragma unroll
+          for (int q = 0; q < ND; ++q) z += ct.D[q * NC + a] * pv[q];
+          y[h * ND + a] += z;
+        }
+      }
+      const int64_t gl = (int64_t)(vd1 - 1) * ND * s1 + (int64_t)j * s1 + ((int64_t)(vd2 - 1) * ND + l) * s2;
+#pragma unroll
+      for (int i = 1; i < WC - 1; ++i)
+        F[c * BOX + box_index<K>(c, i - 1, j, l)] = bu[(int64_t)(oc + i) * sc + gl] - y[i];
+    }
+    // pressure rows: G -= D_c (M M u_c) on the patch cells
+    for (int e = tid; e < NPD * NPD * NPD; e += NT) {
+      const int q0 = e % NPD, q1 = (e / NPD) % NPD, q2 = e / (NPD * NPD);
+      const int qc = c == 0 ? q0 : (c == 1 ? q1 : q2), qd1 = c == 0 ? q1 : q0, qd2 = c == 2 ? q1 : q2;
+      const int h = qc / ND, q = qc % ND;
+      const T* col = Wn + ((h * ND) * WD + ND + qd2) * WD + ND + qd1;
+      T sdot = T(0);
+#pragma unroll
+      for (int a = 0; a < NC; ++a) sdot += ct.D[q * NC + a] * col[a * WD * WD];
+      G[q0 + BX * (q1 + NPD * q2)] -= ct.S[qd1 % ND] * ct.S[qd2 % ND] * sdot;
+    }
+    __syncthreads();
+  }
+}
+
 // Gather, local solve and scatter of patch `blk` of the colour (mode 0) or of
-// coarse column `blk` (mode 1); the body of both patch kernels below.
-template <int K, typename T, bool EO_ALL>
+// coarse column `blk` (mode 1); the body of both patch kernels below.  FUSED
+// (mode 3): the patch residual is computed in the kernel from x_in and b
+// (patch_residual) and the scatter writes x_out = x_in + R_j^T (U, P).
+template <int K, typename T, bool EO_ALL, bool FUSED = false>
 __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk) {
   using C = PatchCfg<K>;
   constexpr int BX = C::BX, BOX = C::BOX, NPD = C::NPD;
@@ -541,7 +699,7 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   }
 
   int v[3];
-  if (A.mode == 0) {
+  if (A.mode == 0 || FUSED) {
     int p = blk;
     for (int d = 0; d < 3; ++d) {
       const int ext = A.part == 1 ? A.cint[d] : A.cnt[d];
@@ -556,7 +714,7 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   PatchGeo g;
   for (int d = 0; d < 3; ++d) g.type[d] = A.mode == 2 ? A.btype[d] : (v[d] == 1 ? 1 : 0) | (v[d] == A.n - 1 ? 2 : 0);
   // the boundary launch skips the interior patches (another launch took them)
-  if (A.mode == 0 && A.part == 2 && g.type[0] == 0 && g.type[1] == 0 && g.type[2] == 0) return;
+  if ((A.mode == 0 || FUSED) && A.part == 2 && g.type[0] == 0 && g.type[1] == 0 && g.type[2] == 0) return;
 
   // SDc = S d per component for the pressure box Dd: (B S) Lam^{-1} (B S)^T d,
   // passes x, y, z then z, y, x; returns the three component boxes to sum
@@ -591,7 +749,18 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   // ---- gather F (velocity boxes in Ba) and G (pressure box in Pp = Ba + 8 BOX);
   // the padded plane (node 2k+1 of the continuous direction) of each velocity
   // box is set to zero.  UG loads per thread are issued before their stores.
-  for (int j0 = tid; j0 < NL; j0 += C::NT * UG) {
+  if constexpr (FUSED) {
+    // the cell matrices live in the Ft boxes (unused until the residual is
+    // done) where they fit, else in static shared memory (k = 1)
+    constexpr int NCT = (int)(sizeof(CellTables<T>) / sizeof(T));
+    constexpr bool IN_FT = NCT <= 3 * BOX;
+    __shared__ T ct_static[IN_FT ? 1 : NCT];
+    T* ctp = IN_FT ? Ft : ct_static;
+    for (int i = tid; i < NCT; i += C::NT) ctp[i] = reinterpret_cast<const T*>(A.ctab)[i];
+    __syncthreads();
+    patch_residual<K, T>(A, v, *reinterpret_cast<const CellTables<T>*>(ctp), Ba, Pp, Bb, R, SD);
+  }
+  for (int j0 = tid; !FUSED && j0 < NL; j0 += C::NT * UG) {
     T val[UG];
     int dst[UG];
 #pragma unroll
@@ -651,7 +820,7 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   // ---- the local Schur system S P = R on mean-free pressures: Direct (a
   // precomputed (S + a 1 1^T)^{-1} of this patch type, which maps a mean-free
   // R to the mean-free solution) or conjugate gradients
-  const T* Mdir = (A.mode == 0 && A.dir) ? A.dir[g.type[0] + 4 * g.type[1] + 16 * g.type[2]] : nullptr;
+  const T* Mdir = ((A.mode == 0 || FUSED) && A.dir) ? A.dir[g.type[0] + 4 * g.type[1] + 16 * g.type[2]] : nullptr;
   if (Mdir) {
     // 16-byte loads where the vectors of a column keep every thread busy
     // (19 % faster at k = 3 in FP32), else one output per load: thread t
@@ -747,13 +916,13 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
         patch_local_decode<K>(j, c, i0, i1, i2);
         const int o = i0 + BX * (i1 + NPD * i2);
         val[u] = (c < 3) ? Bb[c * BOX + o] : Pp[o];
-        gi[u] = A.mode == 0 ? patch_node_global<K>(c, i0, i1, i2, v, A.m) : (int64_t)blk * NL + j;
+        gi[u] = (A.mode == 0 || FUSED) ? patch_node_global<K>(c, i0, i1, i2, v, A.m) : (int64_t)blk * NL + j;
       }
     }
-    if (A.mode == 0) {
+    if (A.mode == 0 || FUSED) {
 #pragma unroll
       for (int u = 0; u < UG; ++u)
-        if (gi[u] >= 0) old[u] = A.x[gi[u]];
+        if (gi[u] >= 0) old[u] = FUSED ? A.xin[gi[u]] : A.x[gi[u]];
 #pragma unroll
       for (int u = 0; u < UG; ++u)
         if (gi[u] >= 0) A.x[gi[u]] = old[u] + val[u];
@@ -765,17 +934,17 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   }
 }
 
-template <int K, typename T>
+template <int K, typename T, bool FUSED = false>
 __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patch_kernel(PatchArgs<T> A) {
-  patch_solve<K, T, false>(A, blockIdx.x);
+  patch_solve<K, T, false, FUSED>(A, blockIdx.x);
 }
 
 // Interior patches only: every 1D eigenbasis is symmetric, so the dense
 // transform code is not compiled in and the kernel's loop stays small in the
 // instruction cache.
-template <int K, typename T>
+template <int K, typename T, bool FUSED = false>
 __global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patch_kernel_interior(PatchArgs<T> A) {
-  patch_solve<K, T, true>(A, blockIdx.x);
+  patch_solve<K, T, true, FUSED>(A, blockIdx.x);
 }
 
 // One colour of several problems of the same degree in one launch: CTA b

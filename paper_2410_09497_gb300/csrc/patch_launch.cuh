@@ -10,17 +10,28 @@ template <int K, typename T>
 cudaError_t launch_patch_k(PatchArgs<T> a, int nblocks, cudaStream_t s) {
   using C = PatchCfg<K>;
   const size_t smem = patch_smem_bytes<K>(sizeof(T));
-  static std::atomic<unsigned long long> smem_set{0}, smem_set_interior{0};
+  static std::atomic<unsigned long long> smem_set{0}, smem_set_interior{0}, smem_set_f{0}, smem_set_fi{0};
+  const bool fused = a.mode == 3;
   {
-    cudaError_t e = allow_dynamic_smem(patch_kernel<K, T>, smem, smem_set);
-    if (e == cudaSuccess) e = allow_dynamic_smem(patch_kernel_interior<K, T>, smem, smem_set_interior);
+    cudaError_t e = fused ? allow_dynamic_smem(patch_kernel<K, T, true>, smem, smem_set_f)
+                          : allow_dynamic_smem(patch_kernel<K, T>, smem, smem_set);
+    if (e == cudaSuccess)
+      e = fused ? allow_dynamic_smem(patch_kernel_interior<K, T, true>, smem, smem_set_fi)
+                : allow_dynamic_smem(patch_kernel_interior<K, T>, smem, smem_set_interior);
     if (e != cudaSuccess) return e;
   }
   if (nblocks > 0) {
-    if (a.mode == 0 && a.part == 1)
+    const bool interior = (a.mode == 0 || fused) && a.part == 1;
+    if (fused) {
+      if (interior)
+        patch_kernel_interior<K, T, true><<<nblocks, C::NT, smem, s>>>(a);
+      else
+        patch_kernel<K, T, true><<<nblocks, C::NT, smem, s>>>(a);
+    } else if (interior) {
       patch_kernel_interior<K, T><<<nblocks, C::NT, smem, s>>>(a);
-    else
+    } else {
       patch_kernel<K, T><<<nblocks, C::NT, smem, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }

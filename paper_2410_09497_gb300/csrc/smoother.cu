@@ -71,6 +71,9 @@ static void fill_common(const stk_problem* P, const Level& L, PatchArgs<T>& a) {
   a.cg_tol_mode = P->opt.local_cg_mode == STK_CG_TOL;
   a.cg_tol = local_tol<T>(P->opt.local_cg_tol);
   a.cols = nullptr;
+  a.xin = nullptr;
+  a.b = nullptr;
+  a.ctab = nullptr;
   a.part = 0;
   a.dir = nullptr;
   for (int d = 0; d < 3; ++d) a.tlo[d] = a.cint[d] = a.btype[d] = 0;
@@ -96,9 +99,14 @@ static void interior_box(int n, int colour, const int* cnt, int* tlo, int* cint)
   }
 }
 
+// One colour of patch solves.  xin == NULL: the patch residuals are read from
+// r (mode 0) and x is updated in place; else they are computed in the kernel
+// from xin and b (mode 3, r is the right-hand side b) and x receives
+// xin + the corrections at the patch DoFs.
 template <typename T>
 static cudaError_t patch_colour(const stk_problem* P, const Level& L, const PatchTables<T>* tab, int colour,
-                                const void* r, void* x, int cg_tol_mode, int cg_iters, double cg_tol) {
+                                const void* r, void* x, int cg_tol_mode, int cg_iters, double cg_tol,
+                                const void* xin = nullptr) {
   int cnt[3];
   colour_counts(L.n, colour, cnt);
   const int nb = cnt[0] * cnt[1] * cnt[2];
@@ -110,6 +118,16 @@ static cudaError_t patch_colour(const stk_problem* P, const Level& L, const Patc
   a.colour = colour;
   for (int d = 0; d < 3; ++d) a.cnt[d] = cnt[d];
   a.mode = 0;
+  if (xin) {
+    a.mode = 3;
+    a.r = nullptr;
+    a.xin = (const T*)xin;
+    a.b = (const T*)r;
+    if constexpr (sizeof(T) == 8)
+      a.ctab = L.tab64;
+    else
+      a.ctab = L.tab32;
+  }
   a.cg_tol_mode = cg_tol_mode;
   a.cg_iters = cg_iters;
   a.cg_tol = local_tol<T>(cg_tol);
@@ -142,6 +160,65 @@ cudaError_t launch_patch_colour_cg(const stk_problem* P, int level, int dtype, i
 cudaError_t launch_patch_colour(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x) {
   return launch_patch_colour_cg(P, level, dtype, colour, r, x, P->opt.local_cg_mode == STK_CG_TOL,
                                 P->opt.local_cg_iters, P->opt.local_cg_tol);
+}
+
+cudaError_t launch_patch_colour_fused(const stk_problem* P, int level, int dtype, int colour, const void* xin,
+                                      const void* b, void* xout) {
+  const Level& L = P->levels[level];
+  const int tolm = P->opt.local_cg_mode == STK_CG_TOL;
+  if (dtype == STK_F64)
+    return patch_colour<double>(P, L, L.ptab64, colour, b, xout, tolm, P->opt.local_cg_iters, P->opt.local_cg_tol,
+                                xin);
+  return patch_colour<float>(P, L, L.ptab32, colour, b, xout, tolm, P->opt.local_cg_iters, P->opt.local_cg_tol, xin);
+}
+
+// x_out = x_in at every entry that no patch of the colour owns: the normal
+// nodes on the patch boundaries, the cells no patch of the colour covers and
+// the constrained entries (the fused colour writes only the patch DoFs).  A
+// cell j along a direction is covered when a vertex v of the colour (v in
+// [1, n-1], v = bit mod 2) has j in {v-1, v}; a continuous-direction node on
+// the cell boundary w is owned only when w is such a vertex (the patch's
+// middle node).
+template <typename T>
+__global__ void copy_unowned_kernel(const T* __restrict__ xin, T* __restrict__ xout, int n, int k, int colour) {
+  const int nd = k + 1, m = n * nd;
+  const int64_t nvel = (int64_t)(m + 1) * m * m, N = 3 * nvel + (int64_t)m * m * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    int c = 3;
+    int64_t loc = e - 3 * nvel;
+    if (e < 3 * nvel) {
+      c = (int)(e / nvel);
+      loc = e - c * nvel;
+    }
+    const int64_t E0 = (c == 0) ? m + 1 : m, E1 = (c == 1) ? m + 1 : m;
+    const int idx[3] = {(int)(loc % E0), (int)((loc / E0) % E1), (int)(loc / (E0 * E1))};
+    bool owned = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int bit = (colour >> d) & 1, i = idx[d];
+      if (d == c) {
+        if (i % nd == 0) {
+          const int w = i / nd;
+          owned = owned && w >= 1 && w <= n - 1 && (w & 1) == bit;
+          continue;
+        }
+      }
+      const int j = min(i / nd, n - 1);
+      const bool cov = (j >= 1 && ((j & 1) == bit)) || (j + 1 <= n - 1 && (((j + 1) & 1) == bit));
+      owned = owned && cov;
+    }
+    if (!owned) xout[e] = xin[e];
+  }
+}
+
+cudaError_t launch_copy_unowned(const stk_problem* P, int level, int dtype, int colour, const void* xin, void* xout) {
+  const Level& L = P->levels[level];
+  const int blocks = (int)std::min<int64_t>((L.ntotal + 255) / 256, 152 * 8);
+  if (dtype == STK_F64)
+    copy_unowned_kernel<double><<<blocks, 256, 0, P->stream>>>((const double*)xin, (double*)xout, L.n, P->k, colour);
+  else
+    copy_unowned_kernel<float><<<blocks, 256, 0, P->stream>>>((const float*)xin, (float*)xout, L.n, P->k, colour);
+  return cudaGetLastError();
 }
 
 template <typename T>

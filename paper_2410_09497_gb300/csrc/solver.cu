@@ -205,26 +205,46 @@ cudaError_t ensure_coarse(stk_problem* P) {
 }
 
 // ---------------------------------------------------------------- smoother
+// Algorithm 2 on one level.  Split form: per colour, r = b - A x over the
+// whole level, then the colour's patch kernel reads R_j r.  Fused form
+// (opt.fused_smoother): the patch kernel computes R_j (b - A x) itself; since
+// all patches of a colour must see the x from before the colour, the colours
+// alternate between x and the level's residual buffer as input and output
+// (x -> tmp -> x ... : eight colours end in x), and the entries no patch of
+// the colour owns are copied across.
 cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void* b) {
   cudaError_t e = ensure_mg_workspace(P, dtype);
   if (e == cudaSuccess && P->opt.local_cg_mode == STK_LOCAL_DIRECT) e = ensure_direct(P, level);
   if (e != cudaSuccess) return e;
   void* r = P->mg[dtype].r[level];
   for (int colour = 0; colour < 8; ++colour) {
-    e = launch_apply(P, level, dtype, x, b, r, -1.0);
-    if (e != cudaSuccess) return e;
-    e = launch_patch_colour(P, level, dtype, colour, r, x);
+    if (P->opt.fused_smoother) {
+      void* xin = (colour % 2 == 0) ? x : r;
+      void* xout = (colour % 2 == 0) ? r : x;
+      e = launch_copy_unowned(P, level, dtype, colour, xin, xout);
+      if (e == cudaSuccess) e = launch_patch_colour_fused(P, level, dtype, colour, xin, b, xout);
+    } else {
+      e = launch_apply(P, level, dtype, x, b, r, -1.0);
+      if (e == cudaSuccess) e = launch_patch_colour(P, level, dtype, colour, r, x);
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// One colour of Algorithm 2: r = b - A x, then the colour's patch solves.
+// One colour of Algorithm 2: r = b - A x, then the colour's patch solves
+// (fused form: x is copied to the residual buffer, which is the colour's input).
 cudaError_t run_smooth_colour(stk_problem* P, int level, int dtype, int colour, void* x, const void* b) {
   cudaError_t e = ensure_mg_workspace(P, dtype);
   if (e == cudaSuccess && P->opt.local_cg_mode == STK_LOCAL_DIRECT) e = ensure_direct(P, level);
   if (e != cudaSuccess) return e;
   void* r = P->mg[dtype].r[level];
+  if (P->opt.fused_smoother) {
+    const size_t bytes = (size_t)P->levels[level].ntotal * (dtype == STK_F64 ? 8 : 4);
+    e = cudaMemcpyAsync(r, x, bytes, cudaMemcpyDeviceToDevice, P->stream);
+    if (e == cudaSuccess) e = launch_patch_colour_fused(P, level, dtype, colour, r, b, x);
+    return e;
+  }
   e = launch_apply(P, level, dtype, x, b, r, -1.0);
   if (e == cudaSuccess) e = launch_patch_colour(P, level, dtype, colour, r, x);
   return e;

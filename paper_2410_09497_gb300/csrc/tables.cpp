@@ -211,4 +211,48 @@ void fill_cell_tables(const Tables1D& t, CellTables<T>* out) {
 template void fill_cell_tables<double>(const Tables1D&, CellTables<double>*);
 template void fill_cell_tables<float>(const Tables1D&, CellTables<float>*);
 
+// Even-odd contraction tables (see ContractTables): built from the dense
+// blocks in double precision; the reflection symmetries of KC, MC and D hold
+// to rounding, so this is the same linear map.
+template <typename T>
+void fill_contract_tables(const Tables1D& t, ContractTables<T>* out) {
+  const int nc = t.k + 2, nd = t.k + 1;
+  const int P = nc / 2, Q = nd / 2;
+  const bool cenc = nc % 2 == 1, cend = nd % 2 == 1;
+  *out = ContractTables<T>{};
+  auto KC = [&](int i, int a) { return t.KC[i * nc + a]; };
+  auto MC = [&](int i, int a) { return t.MC[i * nc + a]; };
+  auto D = [&](int q, int a) { return t.D[q * nc + a]; };
+  for (int i = 0; i < P + (cenc ? 1 : 0); ++i) {
+    const bool centre = i == P;
+    for (int a = 0; a < P + (cenc ? 1 : 0); ++a) {
+      double ek, em;
+      if (a == P) {  // centre input
+        ek = KC(i, P);
+        em = MC(i, P);
+      } else if (centre) {
+        ek = KC(P, a);
+        em = MC(P, a);
+      } else {
+        ek = 0.5 * (KC(i, a) + KC(i, nc - 1 - a));
+        em = 0.5 * (MC(i, a) + MC(i, nc - 1 - a));
+      }
+      out->EK[i * kMaxC + a] = (T)ek;
+      out->EM[i * kMaxC + a] = (T)em;
+    }
+    for (int q = 0; q < Q; ++q)
+      out->ED[i * kMaxD + q] = (T)(centre ? D(q, P) : 0.5 * (D(q, i) - D(nd - 1 - q, i)));
+    if (centre) continue;
+    for (int a = 0; a < P; ++a) {
+      out->OK[i * kMaxC + a] = (T)(0.5 * (KC(i, a) - KC(i, nc - 1 - a)));
+      out->OM[i * kMaxC + a] = (T)(0.5 * (MC(i, a) - MC(i, nc - 1 - a)));
+    }
+    for (int q = 0; q < Q + (cend ? 1 : 0); ++q)
+      out->OD[i * kMaxD + q] = (T)(q == Q ? D(Q, i) : 0.5 * (D(q, i) + D(nd - 1 - q, i)));
+  }
+}
+
+template void fill_contract_tables<double>(const Tables1D&, ContractTables<double>*);
+template void fill_contract_tables<float>(const Tables1D&, ContractTables<float>*);
+
 }  // namespace stk

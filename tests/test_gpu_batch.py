@@ -14,6 +14,8 @@ from oracle.manufactured import Manufactured, rhs
 from oracle.multigrid import Hierarchy
 from seeded_inputs import manufactured_coefficients
 
+from _parity import check
+
 pytestmark = pytest.mark.gpu
 
 # 2^3- and 3^3-based hierarchies, k = 1..3
@@ -105,7 +107,8 @@ def test_smooth_batch_equals_separate_smoothing(stk, dtype_name):
     dt = torch.float64 if dtype_name == "f64" else torch.float32
     sizes = [(4, -1), (6, -1), (8, -1), (3, -1), (8, 1), (12, 1)]
     s = torch.cuda.Stream()
-    probs = [stk.StokesMG(n, 2, 1.0, stream=s) for n, _ in sizes]
+    # the merged launches run the split form of the smoother (residual apply, then patch kernel)
+    probs = [stk.StokesMG(n, 2, 1.0, stream=s, fused_smoother=False) for n, _ in sizes]
     levels = [P._lvl(l) for P, (_, l) in zip(probs, sizes)]
     xs, bs = [], []
     for i, (P, l) in enumerate(zip(probs, levels)):
@@ -137,7 +140,7 @@ def test_interior_launch_matches_single_kernel(stk, dtype_name):
 
     dt = torch.float64 if dtype_name == "f64" else torch.float32
     s = torch.cuda.Stream()
-    P = stk.StokesMG(64, 2, 1.0, stream=s)
+    P = stk.StokesMG(64, 2, 1.0, stream=s, fused_smoother=False)
     N = P.layout()["n_total"]
     b = torch.from_numpy(random_vector(950, N)).to(dt).cuda()
     x1 = torch.from_numpy(random_vector(951, N)).to(dt).cuda()
@@ -150,3 +153,38 @@ def test_interior_launch_matches_single_kernel(stk, dtype_name):
     err = float((x1 - x2).abs().max() / x2.abs().max())
     assert err <= (1e-13 if dtype_name == "f64" else 1e-6)
     P.close()
+
+
+@pytest.mark.parametrize("n,k", [(2, 3), (3, 2), (4, 1), (6, 4), (8, 2), (6, 5), (64, 3)])
+def test_fused_smoother_equals_split_smoother(stk, n, k):
+    """The fused colour step (patch residual computed inside the patch kernel
+    from the x of before the colour, colours alternating between two buffers,
+    unowned entries copied across) equals the split form (a residual apply
+    of the whole level per colour, then the patch kernel) to rounding, for
+    2^3- and 3^3-based meshes, every degree and the 64^3 level whose
+    interior patches run in their own launch; also the Direct local solver."""
+    import torch
+
+    from seeded_inputs import random_vector
+
+    for mode in (stk.CG_FIXED, stk.LOCAL_DIRECT) if n <= 8 else (stk.CG_FIXED,):
+        fused = stk.StokesMG(n, k, 1.0, local_cg_mode=mode)
+        split = stk.StokesMG(n, k, 1.0, local_cg_mode=mode, fused_smoother=False)
+        N = fused.layout()["n_total"]
+        for dt, bar in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+            # constrained entries carry garbage: both forms must leave them as they are
+            x0 = torch.from_numpy(random_vector(3100 + n + k, N)).to(dt).cuda()
+            b = torch.from_numpy(random_vector(3200 + n + k, N)).to(dt).cuda()
+            xa, xb = x0.clone(), x0.clone()
+            fused.smooth(xa, b)
+            split.smooth(xb, b)
+            torch.cuda.synchronize()
+            check(float((xa - xb).abs().max() / xb.abs().max()), bar, f"mode={mode} {dt}")
+            # one colour alone (the entry point copies x to its input buffer)
+            ya, yb = x0.clone(), x0.clone()
+            fused.smooth_colour(5, ya, b)
+            split.smooth_colour(5, yb, b)
+            torch.cuda.synchronize()
+            check(float((ya - yb).abs().max() / yb.abs().max()), bar, f"colour 5 mode={mode} {dt}")
+        fused.close()
+        split.close()
