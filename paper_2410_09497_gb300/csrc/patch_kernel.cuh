@@ -532,14 +532,17 @@ __device__ __forceinline__ int box_index(int c, int ac, int a1, int a2) {
 //   F (3 boxes): velocity rows of the patch (the gather's layout)
 //   G (1 box):   pressure rows
 //   Wn (4 boxes): window of one component, Pst (1 box): p on the patch
-//   Tb (1 box): t = M_d2 L_d1 u + M_d1 L_d2 u on the patch cross-section
+// Per component one thread marches along c on each line (j, l) of the
+// patch cross-section, with the line's two 1D penalty rows in registers, as
+// the apply kernel does.
 template <int K, typename T>
 __device__ __forceinline__ void patch_residual(const PatchArgs<T>& A, const int* v, const CellTables<T>& ct, T* F,
-                                               T* G, T* Wn, T* Pst, T* Tb) {
+                                               T* G, T* Wn, T* Pst) {
   using C = PatchCfg<K>;
   constexpr int ND = K + 1, NC = K + 2, NPD = C::NPD, BX = C::BX, BOX = C::BOX, NT = C::NT;
   constexpr int WC = 2 * K + 3;  // window nodes along c: the patch's two cells
   constexpr int WD = 4 * ND;     // window nodes along d1, d2: patch cells and one halo cell per side
+  constexpr int UL = 8;          // window loads a thread has in flight
   const int m = A.m, n = A.n, tid = threadIdx.x;
   const int64_t nvel = (int64_t)(m + 1) * m * m, mm = (int64_t)m * m;
   // p on the patch cells, and G = b_p
@@ -564,84 +567,97 @@ __device__ __forceinline__ void patch_residual(const PatchArgs<T>& A, const int*
     // stage the window Wn[(i WD + ll) WD + jj] in global memory order (x
     // fastest); corners (halo in both d1 and d2) are never read; nodes outside
     // the domain and the constrained normal nodes (index 0 or m along c) are 0
-    for (int e = tid; e < WC * WD * WD; e += NT) {
-      int i, jj, ll;
-      if (c == 0) {
-        i = e % WC;
-        const int r = e / WC;
-        jj = r % WD;
-        ll = r / WD;
-      } else if (c == 1) {
-        jj = e % WD;
-        const int r = e / WD;
-        i = r % WC;
-        ll = r / WC;
-      } else {
-        jj = e % WD;
-        const int r = e / WD;
-        ll = r % WD;
-        i = r / WD;
+    for (int e0 = tid; e0 < WC * WD * WD; e0 += NT * UL) {
+      T val[UL];
+      int dst[UL];
+#pragma unroll
+      for (int uu = 0; uu < UL; ++uu) {
+        const int e = e0 + uu * NT;
+        dst[uu] = -1;
+        val[uu] = T(0);
+        if (e < WC * WD * WD) {
+          int i, jj, ll;
+          if (c == 0) {
+            i = e % WC;
+            const int r = e / WC;
+            jj = r % WD;
+            ll = r / WD;
+          } else if (c == 1) {
+            jj = e % WD;
+            const int r = e / WD;
+            i = r % WC;
+            ll = r / WC;
+          } else {
+            jj = e % WD;
+            const int r = e / WD;
+            ll = r % WD;
+            i = r / WD;
+          }
+          const bool hj = jj < ND || jj >= 3 * ND, hl = ll < ND || ll >= 3 * ND;
+          if (!(hj && hl)) {
+            dst[uu] = (i * WD + ll) * WD + jj;
+            const int gc = oc + i, g1 = o1 + jj, g2 = o2 + ll;
+            if (gc > 0 && gc < m && g1 >= 0 && g1 < m && g2 >= 0 && g2 < m) val[uu] = u[gc * sc + g1 * s1 + g2 * s2];
+          }
+        }
       }
-      const bool hj = jj < ND || jj >= 3 * ND, hl = ll < ND || ll >= 3 * ND;
-      if (hj && hl) continue;
-      const int gc = oc + i, g1 = o1 + jj, g2 = o2 + ll;
-      T val = T(0);
-      if (gc > 0 && gc < m && g1 >= 0 && g1 < m && g2 >= 0 && g2 < m) val = u[gc * sc + g1 * s1 + g2 * s2];
-      Wn[(i * WD + ll) * WD + jj] = val;
+#pragma unroll
+      for (int uu = 0; uu < UL; ++uu)
+        if (dst[uu] >= 0) Wn[dst[uu]] = val[uu];
     }
     __syncthreads();
-    // t on the patch cross-section (j, l), every node i along c
-    for (int e = tid; e < WC * NPD * NPD; e += NT) {
-      const int j = e % NPD, l = (e / NPD) % NPD, i = e / (NPD * NPD);
+    // velocity rows: thread per line (j, l) of the cross-section, marching
+    // along c: t = S_d2 L_d1 u + S_d1 L_d2 u and uv = S S u at the 2k+3 nodes,
+    // then the cell matrices KC, MC, D^T of the patch's two cells
+    for (int e = tid; e < NPD * NPD; e += NT) {
+      const int j = e % NPD, l = e / NPD;
       const int jj = ND + j, ll = ND + l;
       const int cj = vd1 - 1 + j / ND, bj = j % ND, cl = vd2 - 1 + l / ND, bl = l % ND;
       const int tj = cj == 0 ? 1 : (cj == n - 1 ? 2 : 0), tl = cl == 0 ? 1 : (cl == n - 1 ? 2 : 0);
-      const T* row = Wn + (i * WD + ll) * WD;
-      T a1 = T(0), a2 = T(0);
+      const T sj = ct.S[bj], sl = ct.S[bl], ss = sj * sl;
+      T r1s[ND], r1lo[ND], r1hi[ND], r2s[ND], r2lo[ND], r2hi[ND];
 #pragma unroll
       for (int q = 0; q < ND; ++q) {
-        a1 += ct.LS[tj][bj * ND + q] * row[jj - bj + q];
-        a1 += ct.LLO[bj * ND + q] * row[jj - bj - ND + q];
-        a1 += ct.LHI[bj * ND + q] * row[jj - bj + ND + q];
+        r1s[q] = sl * ct.LS[tj][bj * ND + q];
+        r1lo[q] = sl * ct.LLO[bj * ND + q];
+        r1hi[q] = sl * ct.LHI[bj * ND + q];
+        r2s[q] = sj * ct.LS[tl][bl * ND + q];
+        r2lo[q] = sj * ct.LLO[bl * ND + q];
+        r2hi[q] = sj * ct.LHI[bl * ND + q];
       }
+      T tv[WC], uv[WC];
 #pragma unroll
-      for (int q = 0; q < ND; ++q) {
-        a2 += ct.LS[tl][bl * ND + q] * Wn[(i * WD + ll - bl + q) * WD + jj];
-        a2 += ct.LLO[bl * ND + q] * Wn[(i * WD + ll - bl - ND + q) * WD + jj];
-        a2 += ct.LHI[bl * ND + q] * Wn[(i * WD + ll - bl + ND + q) * WD + jj];
+      for (int i = 0; i < WC; ++i) {
+        const T* row = Wn + (i * WD + ll) * WD + jj - bj;
+        const T* col = Wn + (i * WD + ll - bl) * WD + jj;
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < ND; ++q) {
+          acc += r1s[q] * row[q] + r1lo[q] * row[q - ND] + r1hi[q] * row[q + ND];
+          acc += r2s[q] * col[q * WD] + r2lo[q] * col[(q - ND) * WD] + r2hi[q] * col[(q + ND) * WD];
+        }
+        tv[i] = acc;
+        uv[i] = ss * Wn[(i * WD + ll) * WD + jj];
       }
-      Tb[(i * NPD + l) * NPD + j] = ct.S[bl] * a1 + ct.S[bj] * a2;
-    }
-    __syncthreads();
-    // contraction along c over the patch's two cells: velocity rows of the
-    // 2k+1 patch-interior nodes of each line (j, l), r = b - A x_in
-    for (int e = tid; e < NPD * NPD; e += NT) {
-      const int j = e % NPD, l = e / NPD;
-      const T ss = ct.S[j % ND] * ct.S[l % ND];
       T y[WC];
 #pragma unroll
       for (int i = 0; i < WC; ++i) y[i] = T(0);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        T uv[NC], tv[NC], pv[ND];
-#pragma unroll
-        for (int a = 0; a < NC; ++a) {
-          uv[a] = ss * Wn[((h * ND + a) * WD + ND + l) * WD + ND + j];
-          tv[a] = Tb[((h * ND + a) * NPD + l) * NPD + j];
-        }
+        T pv[ND];
 #pragma unroll
         for (int q = 0; q < ND; ++q) pv[q] = ss * Pst[box_index<K>(c, h * ND + q, j, l)];
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
           T z = T(0);
 #pragma unroll
-          for (int bb = 0; bb < NC; ++bb) z += ct.KC[a * NC + bb] * uv[bb] + ct.MC[a * NC + bb] * tv[bb];
+          for (int bb = 0; bb < NC; ++bb) z += ct.KC[a * NC + bb] * uv[h * ND + bb] + ct.MC[a * NC + bb] * tv[h * ND + bb];
 #pragma unroll
           for (int q = 0; q < ND; ++q) z += ct.D[q * NC + a] * pv[q];
           y[h * ND + a] += z;
         }
       }
-      const int64_t gl = (int64_t)(vd1 - 1) * ND * s1 + (int64_t)j * s1 + ((int64_t)(vd2 - 1) * ND + l) * s2;
+      const int64_t gl = ((int64_t)(vd1 - 1) * ND + j) * s1 + ((int64_t)(vd2 - 1) * ND + l) * s2;
 #pragma unroll
       for (int i = 1; i < WC - 1; ++i)
         F[c * BOX + box_index<K>(c, i - 1, j, l)] = bu[(int64_t)(oc + i) * sc + gl] - y[i];
@@ -758,7 +774,7 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
     T* ctp = IN_FT ? Ft : ct_static;
     for (int i = tid; i < NCT; i += C::NT) ctp[i] = reinterpret_cast<const T*>(A.ctab)[i];
     __syncthreads();
-    patch_residual<K, T>(A, v, *reinterpret_cast<const CellTables<T>*>(ctp), Ba, Pp, Bb, R, SD);
+    patch_residual<K, T>(A, v, *reinterpret_cast<const CellTables<T>*>(ctp), Ba, Pp, Bb, R);
   }
   for (int j0 = tid; !FUSED && j0 < NL; j0 += C::NT * UG) {
     T val[UG];
