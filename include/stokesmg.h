@@ -80,11 +80,14 @@ typedef struct stk_options {
   void* stream;          /* cudaStream_t used by every call, NULL = default stream     */
   int use_graphs;        /* 1 (default): stk_solve replays its V-cycle as a captured
                             CUDA graph (needs a non-NULL stream); 0: direct launches */
-  int fused_smoother;    /* 1 (default): each colour of the smoother computes its patch
-                            residuals inside the patch kernel from the current x and b
-                            (every coupling across the patch boundary kept); 0: one
-                            residual apply of the whole level per colour first, then
-                            the patch kernel.  Same result up to rounding. */
+  int fused_smoother;    /* 0 (default): each colour of the smoother first computes the
+                            residual of the whole level (one operator apply), then the
+                            patch kernel reads its patches' rows; 1: the patch kernel
+                            computes its patch residual itself from the current x and b
+                            (every coupling across the patch boundary kept).  Same
+                            result up to rounding; on GB300 the default is faster for
+                            every degree and precision (the patch kernel is bound by
+                            shared-memory traffic, which the fused residual adds to). */
 } stk_options;
 
 typedef struct stk_problem stk_problem;
@@ -113,6 +116,37 @@ int stk_default_options(stk_options* opt);
  * allocated by the first call that needs them.  On success *out owns device
  * memory until stk_destroy.  Synchronous. */
 int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out);
+
+/* The same method on the unit square, for the two-dimensional results of
+ * Table 1 (Sec. 3.3): RT_k x DGQ_k on n x n cells (n a power of two, n >= 2,
+ * n (k+1) <= 8192), k in 1..8, vertex patches of 2 x 2 cells in four colours
+ * (Sec. 3.1) with the exact ("Direct", Sec. 3.3) local solver, the embedding
+ * and its transpose as transfers and the exact coarse solve on 2 x 2 cells.
+ * Vector layout [u_x | u_y | p], x fastest: u_x on (m+1) x m nodes
+ * (continuous in x), u_y on m x (m+1) (continuous in y), p on m x m,
+ * m = n (k+1); normal entries on the boundary are constrained to zero.
+ * Every entry point takes the returned problem: stk_layout (n_vel_component
+ * = (m+1) m), stk_apply, stk_apply_stage, stk_residual, stk_prolongate_add,
+ * stk_restrict, stk_smooth (four colours), stk_smooth_colour (colour 0..3),
+ * stk_coarse_solve, stk_vcycle, stk_solve, stk_solve_batch and stk_rhs;
+ * stk_smooth_batch, stk_smooth_static and stk_autotune are three-dimensional
+ * only (STK_EINVAL).  The local_cg options are ignored (the local solver is
+ * exact).  The patch inverses (one per boundary type, built on the host in
+ * FP64, 16 types x (2 (2k+1)(2k+2) + (2k+2)^2)^2 entries in FP64 and FP32)
+ * are shared by every problem of the process with the same device, degree,
+ * viscosity and penalty factor.  Synchronous. */
+int stk_setup_planar(int n, int k, double nu, const stk_options* opt, stk_problem** out);
+
+/* L2 errors ||u - u_h|| and ||(-p) - p_h|| over the unit square of a
+ * two-dimensional discrete solution x (finest level, FP64 device vector)
+ * against the manufactured solution that stk_rhs builds from the same
+ * coefficients (the discrete pressure approximates -p because the velocity
+ * rows carry +(p, div v)), by the (k+3)^2-point Gauss rule of every cell: the
+ * error measure of the paper's accuracy study (Sec. 3.3).  err_u and err_p are
+ * host pointers.  Synchronous; allocates and frees a small device buffer.
+ * STK_EINVAL for a three-dimensional problem or NULL arguments. */
+int stk_planar_errors(stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq,
+                      const double* p_amp, const double* x, double* err_u, double* err_p);
 
 /* Release everything stk_setup allocated (bookkeeping, no counterpart in the
  * paper).  NULL is accepted. */
@@ -318,7 +352,13 @@ int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_cta);
  *   psi_c = sum_t psi_amp[c][t] G_a(x) G_b(y) G_c(z),  G_a(s) = s^2 (1-s)^2 sin(a pi s);
  * p_freq[3][3], p_amp[3] of  p = sum_t p_amp[t] cos(a pi x) cos(b pi y) cos(c pi z).
  * The discrete pressure approximates -p because the velocity rows carry
- * +(p, div v) (eq. `weak_form`).  b is a FP64 device vector, overwritten. */
+ * +(p, div v) (eq. `weak_form`).  b is a FP64 device vector, overwritten.
+ * Two-dimensional problems use the first component's terms as the stream
+ * function, psi = sum_t psi_amp[0][t] G_a(x) G_b(y) with (a, b) =
+ * psi_freq[0][t][0..1], u = (d_y psi, -d_x psi), and p = sum_t p_amp[t]
+ * cos(a pi x) cos(b pi y) with (a, b) = p_freq[t][0..1]: with one term a = b = 1
+ * and p = cos(2 pi x) cos(2 pi y) this is the paper's 2D reference solution
+ * (Sec. 3.3) with the bump G_1 in place of its unstated phi. */
 int stk_rhs(stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq, const double* p_amp,
             double* b);
 

@@ -248,3 +248,42 @@ class PlanarHierarchy(Hierarchy):
 
     def _npress(self, disc):
         return (2 * disc.k + 2) ** 2
+
+
+def planar_reference_solution(x, y):
+    """The 2D reference solution of the module docstring: u = (d_y psi, -d_x psi),
+    psi = phi(x) phi(y) with phi = G_1, and p = cos(2 pi x) cos(2 pi y)."""
+    ux = G(1, x, 0) * G(1, y, 1)
+    uy = -G(1, x, 1) * G(1, y, 0)
+    p = np.cos(2 * math.pi * x) * np.cos(2 * math.pi * y)
+    return ux, uy, p
+
+
+def planar_l2_errors(disc: PlanarDiscretization, vec: np.ndarray):
+    """(||u - u_h||, ||(-p) - p_h||) over the unit square for the reference
+    solution, by the (k+3)^2-point Gauss rule of every cell (the discrete
+    pressure approximates -p: the velocity rows carry +(p, div v))."""
+    k, n, h, m = disc.k, disc.n, disc.h, disc.m
+    xq, wq = gauss_legendre(k + 3)
+    Vc, _ = lagrange(continuous_nodes(k), xq)  # [node, point]
+    Vd, _ = lagrange(discontinuous_nodes(k), xq)
+    W = np.outer(wq, wq) * h * h  # [qy, qx]
+    ux_all = vec[:disc.offsets[1]].reshape(m, m + 1)   # [iy, ix]
+    uy_all = vec[disc.offsets[1]:disc.offsets[2]].reshape(m + 1, m)
+    p_all = vec[disc.offsets[2]:].reshape(m, m)
+    eu = ep = 0.0
+    for cy in range(n):
+        for cx in range(n):
+            X = (cx + xq) * h
+            Y = (cy + xq) * h
+            XX, YY = np.meshgrid(X, Y)  # [qy, qx]
+            ux_c = ux_all[cy * (k + 1):(cy + 1) * (k + 1), cx * (k + 1):cx * (k + 1) + k + 2]  # [b, a]
+            uy_c = uy_all[cy * (k + 1):cy * (k + 1) + k + 2, cx * (k + 1):(cx + 1) * (k + 1)]  # [a, b]
+            p_c = p_all[cy * (k + 1):(cy + 1) * (k + 1), cx * (k + 1):(cx + 1) * (k + 1)]
+            uxh = Vd.T @ ux_c @ Vc       # [qy, qx]
+            uyh = Vc.T @ uy_c @ Vd
+            ph = Vd.T @ p_c @ Vd
+            ux, uy, p = planar_reference_solution(XX, YY)
+            eu += np.sum(W * ((uxh - ux) ** 2 + (uyh - uy) ** 2))
+            ep += np.sum(W * (ph + p) ** 2)
+    return math.sqrt(eu), math.sqrt(ep)

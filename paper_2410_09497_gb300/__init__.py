@@ -75,6 +75,8 @@ def load_library():
     sig = {
         "stk_default_options": (ctypes.c_int, [ctypes.POINTER(Options)]),
         "stk_setup": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "stk_setup_planar": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "stk_planar_errors": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "stk_destroy": (ctypes.c_int, [P]),
         "stk_last_error": (ctypes.c_char_p, [P]),
         "stk_num_levels": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
@@ -179,7 +181,7 @@ class StokesMG:
     def __init__(self, n: int, k: int, nu: float = 1.0, *, precision: int = PREC_FP64, gmres_restart: int = 20,
                  max_iter: int = 200, local_cg_mode: int = CG_FIXED, local_cg_iters: int = 15,
                  local_cg_tol: float = 1e-8, penalty_factor: float = 1.0, use_graphs: bool = True,
-                 fused_smoother: bool = True, stream=None):
+                 fused_smoother: bool = False, dim: int = 3, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -197,7 +199,11 @@ class StokesMG:
         self.stream = s
         opt.stream = ctypes.c_void_p(s.cuda_stream)
         h = ctypes.c_void_p()
-        rc = self.lib.stk_setup(int(n), int(k), float(nu), ctypes.byref(opt), ctypes.byref(h))
+        if dim not in (2, 3):
+            raise ValueError("dim must be 2 or 3")
+        setup = self.lib.stk_setup_planar if dim == 2 else self.lib.stk_setup
+        rc = setup(int(n), int(k), float(nu), ctypes.byref(opt), ctypes.byref(h))
+        self.dim = dim
         if rc != 0:
             raise StokesError(rc, self.lib.stk_last_error(None).decode())
         self.h = h
@@ -341,6 +347,28 @@ class StokesMG:
         self._check(self.lib.stk_rhs(self.h, pf.ctypes.data_as(ip), pa.ctypes.data_as(dp), qf.ctypes.data_as(ip),
                                      qa.ctypes.data_as(dp), self._vec(b, L, F64)))
         return b
+
+    @staticmethod
+    def _coeff_arrays(coeffs):
+        import numpy as np
+
+        pf = np.ascontiguousarray(coeffs["psi_freq"], dtype=np.int32).reshape(-1)
+        pa = np.ascontiguousarray(coeffs["psi_amp"], dtype=np.float64).reshape(-1)
+        qf = np.ascontiguousarray(coeffs["p_freq"], dtype=np.int32).reshape(-1)
+        qa = np.ascontiguousarray(coeffs["p_amp"], dtype=np.float64).reshape(-1)
+        return pf, pa, qf, qa
+
+    def planar_errors(self, coeffs: dict, x):
+        """(||u - u_h||_L2, ||(-p) - p_h||_L2) of a 2D discrete solution x against the
+        manufactured solution of `coeffs` (stk_planar_errors)."""
+        L = self.num_levels - 1
+        pf, pa, qf, qa = self._coeff_arrays(coeffs)
+        ip = ctypes.POINTER(ctypes.c_int)
+        dp = ctypes.POINTER(ctypes.c_double)
+        eu, ep = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.stk_planar_errors(self.h, pf.ctypes.data_as(ip), pa.ctypes.data_as(dp), qf.ctypes.data_as(ip),
+                                               qa.ctypes.data_as(dp), self._vec(x, L, F64), ctypes.byref(eu), ctypes.byref(ep)))
+        return eu.value, ep.value
 
     def solve(self, b, x, rtol: float = 1e-8, check: bool = True):
         """FGMRES + V-cycle solve of A x = b (FP64 vectors); returns an info dict."""

@@ -2,6 +2,7 @@
 // entry points.  Every function returns a status code and never throws.
 #include <cstdio>
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -54,6 +55,10 @@ void free_level(stk::Level& L) {
   L.dirtab64 = nullptr;
   L.dirtab32 = nullptr;
   L.dir_ready = false;
+  if (L.flat64) cudaFree(L.flat64);
+  if (L.flat32) cudaFree(L.flat32);
+  L.flat64 = nullptr;
+  L.flat32 = nullptr;
 }
 
 void free_problem(stk_problem* P) {
@@ -80,6 +85,11 @@ void free_problem(stk_problem* P) {
 
 int check_dtype(stk_problem* P, int dtype) {
   if (dtype != STK_F64 && dtype != STK_F32) return fail(P, STK_EINVAL, "dtype must be STK_F64 or STK_F32");
+  return STK_OK;
+}
+
+int check_3d(stk_problem* P, const char* what) {
+  if (P->dim != 3) return fail(P, STK_EINVAL, std::string(what) + " is not available for two-dimensional problems");
   return STK_OK;
 }
 
@@ -110,7 +120,7 @@ int stk_default_options(stk_options* opt) {
   opt->penalty_factor = 1.0;
   opt->stream = nullptr;
   opt->use_graphs = 1;
-  opt->fused_smoother = 1;
+  opt->fused_smoother = 0;
   return STK_OK;
 }
 
@@ -259,6 +269,94 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
   return STK_OK;
 }
 
+int stk_setup_planar(int n, int k, double nu, const stk_options* opt, stk_problem** out) {
+  if (!out) return fail(nullptr, STK_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (k < 1 || k > stk::kMaxPlanarDegree) return fail(nullptr, STK_EINVAL, "degree k must be in 1..8");
+  if (!(nu > 0.0)) return fail(nullptr, STK_EINVAL, "viscosity must be positive");
+  if (n < 2 || (n & (n - 1)) != 0) return fail(nullptr, STK_EINVAL, "n must be a power of two (n >= 2)");
+  if ((int64_t)n * (k + 1) > 8192) return fail(nullptr, STK_EINVAL, "mesh too large");
+  stk_problem* P = new (std::nothrow) stk_problem();
+  if (!P) return fail(nullptr, STK_ENOMEM, "host allocation failed");
+  P->dim = 2;
+  P->k = k;
+  P->nu = nu;
+  if (opt)
+    P->opt = *opt;
+  else
+    stk_default_options(&P->opt);
+  if (!(P->opt.penalty_factor > 0.0) || P->opt.gmres_restart < 1 || P->opt.gmres_restart > 60 ||
+      P->opt.max_iter < 1 || (P->opt.precision != STK_PREC_FP64 && P->opt.precision != STK_PREC_MIXED)) {
+    delete P;
+    return fail(nullptr, STK_EINVAL, "invalid options (penalty > 0, restart in 1..60, max_iter >= 1, known precision)");
+  }
+  P->stream = reinterpret_cast<cudaStream_t>(P->opt.stream);
+  std::vector<int> sizes;
+  for (int s2 = n; s2 >= 2; s2 /= 2) sizes.push_back(s2);
+  P->levels.resize(sizes.size());
+  try {
+    for (size_t i = 0; i < sizes.size(); ++i) {
+      stk::Level& L = P->levels[sizes.size() - 1 - i];
+      L.n = sizes[i];
+      L.m = L.n * (k + 1);
+      L.h = 1.0 / L.n;
+      L.nvel = (int64_t)(L.m + 1) * L.m;
+      L.npress = (int64_t)L.m * L.m;
+      L.ntotal = 2 * L.nvel + L.npress;
+      L.t1d = stk::build_tables(k, L.h, nu, P->opt.penalty_factor);
+    }
+  } catch (const std::bad_alloc&) {
+    delete P;
+    return fail(nullptr, STK_ENOMEM, "host allocation failed");
+  }
+  cudaError_t e = stk::setup_planar(P);
+  if (e == cudaSuccess) {
+    const std::vector<double> xt = stk::build_transfer_tables(k);
+    std::vector<float> xt32(xt.begin(), xt.end());
+    const std::vector<double>& S = P->levels.back().t1d.S;
+    e = stk::dev_alloc(&P->xfer64, sizeof(double) * xt.size());
+    if (e == cudaSuccess) e = stk::dev_alloc(&P->xfer32, sizeof(float) * xt.size());
+    if (e == cudaSuccess) e = stk::dev_alloc(&P->pmean_w, sizeof(double) * S.size());
+    if (e == cudaSuccess) e = cudaMemcpy(P->xfer64, xt.data(), sizeof(double) * xt.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->xfer32, xt32.data(), sizeof(float) * xt.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->pmean_w, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    std::string msg = std::string("setup_planar: ") + cudaGetErrorString(e);
+    free_problem(P);
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA, msg);
+  }
+  *out = P;
+  return STK_OK;
+}
+
+int stk_planar_errors(stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq,
+                      const double* p_amp, const double* x, double* err_u, double* err_p) {
+  if (!P) return STK_EINVAL;
+  if (P->dim != 2) return fail(P, STK_EINVAL, "planar_errors needs a two-dimensional problem");
+  if (!psi_freq || !psi_amp || !p_freq || !p_amp || !err_u || !err_p)
+    return fail(P, STK_EINVAL, "NULL argument");
+  int rc = check_vec(P, x, "x");
+  if (rc) return rc;
+  constexpr int kBlocks = 304;
+  double* part = nullptr;
+  cudaError_t e = stk::dev_alloc(&part, sizeof(double) * 2 * kBlocks);
+  if (e == cudaSuccess) e = stk::launch_errors_planar(P, psi_freq, psi_amp, p_freq, p_amp, x, part, kBlocks);
+  std::vector<double> h(2 * kBlocks, 0.0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * kBlocks, cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (part) cudaFree(part);
+  if (e != cudaSuccess) return status_of(P, e, "planar_errors");
+  double su = 0.0, sp = 0.0;
+  for (int b = 0; b < kBlocks; ++b) {
+    su += h[2 * b];
+    sp += h[2 * b + 1];
+  }
+  *err_u = std::sqrt(su);
+  *err_p = std::sqrt(sp);
+  return STK_OK;
+}
+
 int stk_destroy(stk_problem* P) {
   if (!P) return STK_OK;
   cudaStreamSynchronize(P->stream);
@@ -348,7 +446,8 @@ int stk_smooth_colour(stk_problem* P, int level, int dtype, int colour, void* x,
   int rc = check_level(P, level);
   if (rc) return rc;
   if ((rc = check_dtype(P, dtype)) || (rc = check_vec(P, x, "x")) || (rc = check_vec(P, b, "b"))) return rc;
-  if (colour < 0 || colour > 7) return fail(P, STK_EINVAL, "colour must be in 0..7");
+  if (colour < 0 || colour >= (P->dim == 2 ? 4 : 8))
+    return fail(P, STK_EINVAL, P->dim == 2 ? "colour must be in 0..3" : "colour must be in 0..7");
   if (x == b) return fail(P, STK_EINVAL, "x and b must not alias");
   return status_of(P, stk::run_smooth_colour(P, level, dtype, colour, x, b), "smooth_colour");
 }
@@ -360,6 +459,7 @@ int stk_smooth_batch(stk_problem* const* problems, int count, const int* levels,
   for (int i = 0; i < count; ++i) {
     stk_problem* P = problems[i];
     if (!P) return fail(nullptr, STK_EINVAL, "smooth_batch: NULL problem");
+    if (P->dim != 3) return fail(nullptr, STK_EINVAL, "smooth_batch: three-dimensional problems only");
     if (P->k != problems[0]->k) return fail(nullptr, STK_EINVAL, "smooth_batch: problems of different degrees");
     int rc;
     if ((rc = check_level(P, levels[i])) || (rc = check_vec(P, x[i], "x")) || (rc = check_vec(P, b[i], "b"))) {
@@ -431,7 +531,9 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
 
 int stk_autotune(stk_problem* P, int dtype) {
   if (!P) return STK_EINVAL;
-  int rc = check_dtype(P, dtype);
+  int rc = check_3d(P, "autotune");
+  if (rc) return rc;
+  rc = check_dtype(P, dtype);
   if (rc) return rc;
   const size_t es = dtype == STK_F64 ? 8 : 4;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -495,6 +597,7 @@ int stk_rhs(stk_problem* P, const int* psi_freq, const double* psi_amp, const in
     if (psi_freq[i] < 1 || psi_freq[i] > 8) return fail(P, STK_EINVAL, "psi frequencies must be in 1..8");
   for (int i = 0; i < 9; ++i)
     if (p_freq[i] < 1 || p_freq[i] > 8) return fail(P, STK_EINVAL, "pressure frequencies must be in 1..8");
+  if (P->dim == 2) return status_of(P, stk::launch_rhs_planar(P, psi_freq, psi_amp, p_freq, p_amp, b), "rhs");
   return status_of(P, stk::launch_rhs(P, psi_freq, psi_amp, p_freq, p_amp, b), "rhs");
 }
 

@@ -465,6 +465,10 @@ static cudaError_t dispatch_apply(int k, const Level& L, const CellTables<T>& ta
 
 cudaError_t launch_apply_on(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
                             double alpha, int stages, cudaStream_t stream) {
+  if (P->dim == 2) {
+    if (b ? alpha != -1.0 : alpha != 1.0) return cudaErrorInvalidValue;
+    return launch_apply_planar(P, level, dtype, x, b, y, stages, stream);
+  }
   const Level& L = P->levels[level];
   if (dtype == STK_F64)
     return dispatch_apply<double>(P->k, L, L.htab64, L.hce64, (const double*)x, (const double*)b, (double*)y, alpha,

@@ -194,7 +194,28 @@ struct Level {
   float* dirM32 = nullptr;
   const double** dirtab64 = nullptr;
   const float** dirtab32 = nullptr;
+  // two dimensions: the 1D cell tables flattened with runtime sizes (the
+  // order of stk_cell_tables), device copies in both precisions
+  double* flat64 = nullptr;
+  float* flat32 = nullptr;
 };
+
+// Exact local solver of the 2D vertex patches (2 x 2 cells): for every patch
+// type (boundary type t0 + 4 t1 per direction) the pseudo-inverse of the patch
+// matrix with the pressure mean fixed, at h = 1 (the velocity block does not
+// depend on h in two dimensions and the divergence blocks scale with h; the
+// kernels rescale the pressure rows and columns by 1/h), column-major, FP64
+// and FP32.  Shared by the problems of a process with the same device,
+// degree, viscosity and penalty factor.
+struct PlanarInverses {
+  int nloc = 0;
+  double* m64[16] = {};
+  float* m32[16] = {};
+  const double** tab64 = nullptr;  // device arrays of the 16 pointers
+  const float** tab32 = nullptr;
+  ~PlanarInverses();
+};
+constexpr int kMaxPlanarDegree = 8;
 
 struct MgWork {
   bool ready = false;
@@ -217,6 +238,7 @@ struct Coarse3Factors;  // coarse3.cu
 }  // namespace stk
 
 struct stk_problem {
+  int dim = 3;  // 3: the unit cube; 2: the unit square (Table 1)
   int k = 0;
   double nu = 1.0;
   stk_options opt{};
@@ -228,6 +250,7 @@ struct stk_problem {
   double* coarse_inv = nullptr;    // dense pseudo-inverse of the 2^3 coarse problem, patch order
   double* coarse3[3] = {nullptr, nullptr, nullptr};  // FP64 b, x, r of a 3^3 coarse mesh
   std::shared_ptr<stk::Coarse3Factors> coarse3f;      // dense factors of the 3^3 coarse problem (shared)
+  std::shared_ptr<stk::PlanarInverses> pinv2;         // 2D patch inverses (shared)
   stk::MgWork mg[2];               // [STK_F64], [STK_F32]
   stk::KrylovWork kry;
   std::string err;
@@ -289,5 +312,19 @@ int run_solve_batch(stk_problem* const* Ps, int count, const double* const* b, d
 // rhs.cu
 cudaError_t launch_rhs(const stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq,
                        const double* p_amp, double* b);
+// planar.cu: the method on the unit square (n = 2^L cells per side, k = 1..8)
+cudaError_t setup_planar(stk_problem* P);
+cudaError_t launch_apply_planar(const stk_problem* P, int level, int dtype, const void* x, const void* b, void* y,
+                                int stages, cudaStream_t s);
+cudaError_t launch_prolongate_add_planar(const stk_problem* P, int fine_level, int dtype, const void* xc, void* xf);
+cudaError_t launch_restrict_planar(const stk_problem* P, int fine_level, int dtype, const void* rf, void* rc);
+// one colour of 2D patch solves (exact local solver): x += R_j^T A_j^+ R_j r
+cudaError_t launch_patch_colour_planar(const stk_problem* P, int level, int dtype, int colour, const void* r, void* x);
+cudaError_t launch_coarse_solve_planar(const stk_problem* P, int dtype, const void* b, void* x);
+cudaError_t launch_pressure_mean_planar(stk_problem* P, double* x, double* partial, int nblocks);
+cudaError_t launch_rhs_planar(const stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq,
+                              const double* p_amp, double* b);
+cudaError_t launch_errors_planar(const stk_problem* P, const int* psi_freq, const double* psi_amp, const int* p_freq,
+                                 const double* p_amp, const double* x, double* partial, int nblocks);
 
 }  // namespace stk

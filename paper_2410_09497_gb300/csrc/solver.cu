@@ -179,6 +179,7 @@ cudaError_t ensure_mg_workspace(stk_problem* P, int dtype) {
 }
 
 cudaError_t ensure_coarse(stk_problem* P) {
+  if (P->dim == 2) return cudaSuccess;  // the 2D coarse solve uses the patch inverses built at setup
   if (P->levels[0].n != 2) {
     // 3^3 coarse mesh: FP64 vectors and the dense block factors
     if (P->coarse3f) return cudaSuccess;
@@ -214,6 +215,15 @@ cudaError_t ensure_coarse(stk_problem* P) {
 // the colour owns are copied across.
 cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void* b) {
   cudaError_t e = ensure_mg_workspace(P, dtype);
+  if (P->dim == 2) {  // four colours, exact local solver, split form
+    if (e != cudaSuccess) return e;
+    void* r = P->mg[dtype].r[level];
+    for (int colour = 0; colour < 4 && e == cudaSuccess; ++colour) {
+      e = launch_apply(P, level, dtype, x, b, r, -1.0);
+      if (e == cudaSuccess) e = launch_patch_colour_planar(P, level, dtype, colour, r, x);
+    }
+    return e;
+  }
   if (e == cudaSuccess && P->opt.local_cg_mode == STK_LOCAL_DIRECT) e = ensure_direct(P, level);
   if (e != cudaSuccess) return e;
   void* r = P->mg[dtype].r[level];
@@ -236,6 +246,13 @@ cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void
 // (fused form: x is copied to the residual buffer, which is the colour's input).
 cudaError_t run_smooth_colour(stk_problem* P, int level, int dtype, int colour, void* x, const void* b) {
   cudaError_t e = ensure_mg_workspace(P, dtype);
+  if (P->dim == 2) {
+    if (e != cudaSuccess) return e;
+    void* r2 = P->mg[dtype].r[level];
+    e = launch_apply(P, level, dtype, x, b, r2, -1.0);
+    if (e == cudaSuccess) e = launch_patch_colour_planar(P, level, dtype, colour, r2, x);
+    return e;
+  }
   if (e == cudaSuccess && P->opt.local_cg_mode == STK_LOCAL_DIRECT) e = ensure_direct(P, level);
   if (e != cudaSuccess) return e;
   void* r = P->mg[dtype].r[level];
@@ -313,6 +330,7 @@ __global__ void __launch_bounds__(256) remove_pressure_sum(double* __restrict__ 
 }
 
 static cudaError_t coarse_level_solve(stk_problem* P, int dtype, const void* b, void* x) {
+  if (P->dim == 2) return launch_coarse_solve_planar(P, dtype, b, x);
   if (P->levels[0].n == 2) return launch_coarse_solve(P, dtype, b, x);
   const int64_t n = P->levels[0].ntotal;
   double *cb = P->coarse3[0], *cx = P->coarse3[1];
@@ -439,6 +457,7 @@ static cudaError_t precondition(stk_problem* P, const double* v, double* z) {
 }
 
 cudaError_t project_pressure_mean(stk_problem* P, double* x) {
+  if (P->dim == 2) return launch_pressure_mean_planar(P, x, P->kry.partial, kRedBlocks);
   const Level& L = P->levels.back();
   double* p = x + 3 * L.nvel;
   pressure_mean_partial<<<kRedBlocks, kRedThreads, 0, P->stream>>>(p, L.m, P->k + 1, P->pmean_w, P->kry.partial);

@@ -59,6 +59,10 @@ cudaError_t scratch_address(void** out) {
 
 extern "C" int stk_smooth_static(stk_problem* P, int level, int dtype, void* x, const void* b) {
   if (!P) return STK_EINVAL;
+  if (P->dim != 3) {
+    P->err = "smooth_static: three-dimensional problems only";
+    return STK_EINVAL;
+  }
   if (level < 0 || level >= (int)P->levels.size()) {
     P->err = "level out of range";
     return STK_EINVAL;

@@ -198,6 +198,7 @@ static cudaError_t dispatch_xfer(bool prolong, int k, const T* in, T* out, const
 }
 
 cudaError_t launch_prolongate_add(const stk_problem* P, int fine_level, int dtype, const void* xc, void* xf) {
+  if (P->dim == 2) return launch_prolongate_add_planar(P, fine_level, dtype, xc, xf);
   const Level& C = P->levels[fine_level - 1];
   if (dtype == STK_F64)
     return dispatch_xfer<double>(true, P->k, (const double*)xc, (double*)xf, P->xfer64, C.n, P->stream);
@@ -205,6 +206,7 @@ cudaError_t launch_prolongate_add(const stk_problem* P, int fine_level, int dtyp
 }
 
 cudaError_t launch_restrict(const stk_problem* P, int fine_level, int dtype, const void* rf, void* rc) {
+  if (P->dim == 2) return launch_restrict_planar(P, fine_level, dtype, rf, rc);
   const Level& C = P->levels[fine_level - 1];
   const size_t bytes = (size_t)C.ntotal * (dtype == STK_F64 ? 8 : 4);
   cudaError_t e = cudaMemsetAsync(rc, 0, bytes, P->stream);

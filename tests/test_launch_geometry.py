@@ -237,3 +237,46 @@ def test_transfer_index_maps(nc, k):
     # restriction: at most two atomic contributions onto zero (order independent)
     assert (coarse_adds[free_c] >= 1).all() and coarse_adds.max() <= 2
     assert (coarse_adds[~free_c] == 0).all()
+
+
+def _planar_patch_global(j, v0, v1, k, m):
+    """The 2D patch kernel's patch-local to global map (planar.cu), restated."""
+    nd, npc, npd = k + 1, 2 * k + 1, 2 * k + 2
+    nv, nvel = npc * npd, (m + 1) * m
+    if j < nv:
+        ix, iy = j % npc, j // npc
+        return ((v0 - 1) * nd + 1 + ix) + (m + 1) * ((v1 - 1) * nd + iy)
+    if j < 2 * nv:
+        jj = j - nv
+        ix, iy = jj % npd, jj // npd
+        return nvel + ((v0 - 1) * nd + ix) + m * ((v1 - 1) * nd + 1 + iy)
+    jj = j - 2 * nv
+    ix, iy = jj % npd, jj // npd
+    return 2 * nvel + ((v0 - 1) * nd + ix) + m * ((v1 - 1) * nd + iy)
+
+
+@pytest.mark.parametrize("n,k", [(2, 1), (4, 3), (8, 2), (4, 8)])
+def test_planar_patch_map_matches_oracle_patches(n, k):
+    """The 2D patch kernel's block-to-vertex decode and patch-local map give
+    the oracle's colour vertices and patch DoF sets: in bounds, no constrained
+    entry, disjoint within a colour."""
+    from oracle.planar import PlanarDiscretization, planar_colour_vertices, planar_patch_dofs
+
+    d = PlanarDiscretization(n, k)
+    m, nloc = n * (k + 1), 2 * (2 * k + 1) * (2 * k + 2) + (2 * k + 2) ** 2
+    free = d.free_mask()
+    for colour in range(4):
+        cnt0 = n // 2 if colour & 1 else (n - 1) // 2
+        cnt1 = n // 2 if colour & 2 else (n - 1) // 2
+        verts = []
+        for blk in range(cnt0 * cnt1):
+            t0, t1 = blk % cnt0, blk // cnt0
+            verts.append((2 * t0 + 1 if colour & 1 else 2 * t0 + 2, 2 * t1 + 1 if colour & 2 else 2 * t1 + 2))
+        assert verts == planar_colour_vertices(n, colour)
+        seen = set()
+        for v in verts:
+            g = [_planar_patch_global(j, v[0], v[1], k, m) for j in range(nloc)]
+            assert sorted(g) == sorted(planar_patch_dofs(d, v).tolist())
+            assert all(0 <= x < d.N and free[x] for x in g)
+            assert not seen.intersection(g)
+            seen.update(g)

@@ -123,3 +123,34 @@ def test_table1_fractional_iteration_counts():
         assert abs(nu[4, k] - nu[3, k]) <= 0.4
     for L in (3, 4):
         assert nu[L, 5] < nu[L, 3]
+
+
+def test_planar_l2_errors_converge_at_the_optimal_rate():
+    """The 2D error measure (the accuracy study of Sec. 3.3): for the reference
+    solution, solved to 1e-12, the velocity and pressure L2 errors fall by
+    2^(k+1) per refinement (textbook best approximation of Q_{k+1} / Q_k
+    fields), and the interpolation-free zero vector has the exact solution's
+    norms as its errors."""
+    import math
+
+    from oracle.planar import planar_l2_errors, planar_reference_solution
+    from oracle.basis import gauss_legendre
+
+    k = 2
+    errs = []
+    for n in (4, 8):
+        H = PlanarHierarchy(n, k, local="lu")
+        d = H.levels[-1].disc
+        x, _ = H.solve(d.rhs(), tol=1e-12)
+        errs.append(planar_l2_errors(d, x))
+    for a, b in zip(errs[0], errs[1]):
+        assert math.log2(a / b) >= k + 1 - 0.3
+    # the zero vector: ||u|| and ||p|| of the reference solution by a fine tensor Gauss rule
+    d = PlanarDiscretization(8, 3)  # 6 Gauss points per direction on cells of 1/8: exact to rounding here
+    eu, ep = planar_l2_errors(d, np.zeros(d.N))
+    xq, wq = gauss_legendre(40)
+    X, Y = np.meshgrid(xq, xq)
+    ux, uy, p = planar_reference_solution(X, Y)
+    W = np.outer(wq, wq)
+    assert abs(eu - math.sqrt(np.sum(W * (ux ** 2 + uy ** 2)))) <= 1e-12
+    assert abs(ep - 0.5) <= 1e-12  # ||cos(2 pi x) cos(2 pi y)|| = 1/2
