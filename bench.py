@@ -416,6 +416,72 @@ def run_batch(args):
                                           "per colour for all problems of a degree"}}
 
 
+PLANAR_REFERENCE = {  # the paper's 2D reference solution: psi = G_1(x) G_1(y), p = cos(2 pi x) cos(2 pi y)
+    "psi_freq": [[[1, 1, 1]] * 3] * 3, "psi_amp": [[1.0, 0.0, 0.0]] * 3,
+    "p_freq": [[2, 2, 1], [1, 1, 1], [1, 1, 1]], "p_amp": [1.0, 0.0, 0.0]}
+
+# Table 1 (Sec. 3.3), Direct solver columns Q_3 .. Q_8, rows L = 3 .. 9: the
+# paper's printed fractional GMRES counts in two dimensions (context for the
+# GPU counts of the same problems)
+TABLE1_DIRECT = {3: [2.8, 2.4, 2.1, 2.2, 1.9, 2.1], 4: [3.2, 2.4, 2.3, 2.2, 2.1, 2.0], 5: [3.2, 2.3, 2.3, 2.0, 2.0, 1.9],
+                 6: [3.0, 2.2, 2.2, 1.9, 1.9, 1.8], 7: [2.9, 1.9, 1.9, 1.8, 1.8, 1.7], 8: [2.8, 1.9, 1.8, 1.8, 1.8, 1.8],
+                 9: [2.7, 1.9, 1.9, 1.8, 1.8, 1.8]}
+
+
+def run_planar(args, stream):
+    """The two-dimensional results on the GPU: Table 1 (fractional FGMRES
+    counts to 1e-8 with the exact local solver, mixed precision, the paper's
+    reference solution, L = 3 .. planar_L, Q_3 .. Q_8) and the accuracy study
+    (velocity and pressure L2 errors against the time to solution, k = 2..5)."""
+    import torch
+
+    from paper_2410_09497_gb300 import PREC_MIXED, StokesMG
+
+    table, diffs = {}, []
+    with torch.cuda.stream(stream):
+        for L in range(3, args.planar_L + 1):
+            row = {}
+            for k in range(3, 9):
+                n = 2 ** L
+                P = StokesMG(n, k, 1.0, dim=2, precision=PREC_MIXED, stream=stream)
+                b = torch.empty(P.layout()["n_total"], dtype=torch.float64, device="cuda")
+                P.rhs(PLANAR_REFERENCE, b)
+                x = torch.zeros_like(b)
+                P.solve(b, x, 1e-8)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = P.solve(b, x, 1e-8)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                P.close()
+                row[f"Q{k}"] = {"nu": round(info["nu"], 3), "iterations": info["iterations"],
+                                "paper": TABLE1_DIRECT[L][k - 3], "seconds": dt, "dofs": int(b.numel())}
+                diffs.append(info["nu"] - TABLE1_DIRECT[L][k - 3])
+            table[str(L)] = row
+        study = []
+        for k in (2, 3, 4, 5):
+            for L in range(3, args.planar_L + 1):
+                n = 2 ** L
+                P = StokesMG(n, k, 1.0, dim=2, precision=PREC_MIXED, stream=stream)
+                b = torch.empty(P.layout()["n_total"], dtype=torch.float64, device="cuda")
+                P.rhs(PLANAR_REFERENCE, b)
+                x = torch.zeros_like(b)
+                P.solve(b, x, 1e-8)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                P.solve(b, x, 1e-8)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                eu, ep = P.planar_errors(PLANAR_REFERENCE, x)
+                study.append({"k": k, "n": n, "dofs": int(b.numel()), "seconds": dt, "err_u": eu, "err_p": ep})
+                P.close()
+    return {"workload": "2D Stokes, unit square, RT_k x DGQ_k, reference solution of the paper, FGMRES(20) + "
+                        "V-cycle (exact local solver, FP32 V-cycle) to 1e-8",
+            "table1": table, "mean_nu_minus_paper": sum(diffs) / len(diffs),
+            "max_abs_nu_minus_paper": max(abs(d) for d in diffs),
+            "accuracy_vs_time": study}
+
+
 def run_sweep(args, stream):
     """FP64 apply throughput over the degrees k = 1..5 on an n^3 mesh (the
     operator sweep); L2 is flushed between timed applies when x and y fit in it."""
@@ -724,6 +790,8 @@ def run_ours(args):
         line["solve"] = run_solve_pair(args, stream, ws)
     if args.batch > 0:
         line["batch"] = run_batch(args)
+    if args.planar_L >= 3:
+        line["planar"] = run_planar(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         base = oracle_spmv_baselines(8, k, args.cpu_seconds / 2)
         line["cpu_baseline"] = base["all"]
@@ -757,6 +825,7 @@ def main():
     ap.add_argument("--sweep-n", type=int, default=64, help="mesh of the FP64 apply sweep over k = 1..5 (0: skip)")
     ap.add_argument("--smooth-n", type=int, default=64, help="mesh of the smoothing-step sub-benchmark (0: skip)")
     ap.add_argument("--batch", type=int, default=64, help="batched uneven solves (0: skip)")
+    ap.add_argument("--planar-L", type=int, default=8, help="finest level of the 2D Table 1 and accuracy study (0: skip)")
     ap.add_argument("--mode", default="apply", choices=["apply", "smooth", "solve"],
                     help="apply: the benchmark line; smooth / solve: time smoothing steps or one "
                          "mixed-precision solve only (profiling)")

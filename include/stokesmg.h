@@ -334,11 +334,19 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
 /* Autotuner (no counterpart in the paper): for every level, time the operator
  * apply in `dtype` with each candidate march length of its velocity kernel
  * (cells per CTA: n, n/2, ..., 2) on the problem's stream and keep the
- * fastest; every later apply, residual, smoothing step and solve of that dtype
- * uses it (a V-cycle graph that an earlier solve captured in that dtype is
- * discarded, so the next solve captures the tuned launches).  Synchronous;
- * allocates and frees two vectors per level. */
+ * fastest, then, on every level that is smoothed, one smoothing step in each
+ * form (fused_smoother 0 and 1, with the problem's local solver) and keep
+ * the faster; every later apply, residual, smoothing step and solve of that
+ * dtype uses them (a V-cycle graph that an earlier solve captured in that
+ * dtype is discarded, so the next solve captures the tuned launches).
+ * Synchronous; allocates and frees two vectors per level (and builds the
+ * Direct local inverses of a level if that is the local solver). */
 int stk_autotune(stk_problem* P, int dtype);
+
+/* The smoother form chosen by stk_autotune for a level and dtype: 0 split,
+ * 1 fused, -1 not tuned (stk_options.fused_smoother applies); no counterpart
+ * in the paper. */
+int stk_tuned_smoother(const stk_problem* P, int level, int dtype, int* fused);
 
 /* The march length chosen by stk_autotune for a level and dtype (0 = not
  * tuned: the built-in choice is used); no counterpart in the paper. */

@@ -95,6 +95,7 @@ def load_library():
         "stk_smooth_colour": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
         "stk_autotune": (ctypes.c_int, [P, ctypes.c_int]),
         "stk_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "stk_tuned_smoother": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_smooth_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P)]),
         "stk_patch_eigen": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -310,14 +311,17 @@ class StokesMG:
         self._check(self.lib.stk_smooth_static(self.h, level, dt, self._vec(x, level), self._vec(b, level, dt)))
         return x
 
-    def autotune(self, dtype: int = F32):
-        """Time the apply's march length per level for dtype and keep the fastest; returns {level: cells_per_cta}."""
+    def autotune(self, dtype: int = F32, with_smoother: bool = False):
+        """Time the apply's march length per level (and the smoother's form on the
+        smoothed levels) for dtype and keep the fastest; returns {level: cells_per_cta}
+        or, with with_smoother, {level: (cells_per_cta, fused)}."""
         self._check(self.lib.stk_autotune(self.h, int(dtype)))
         out = {}
         for level in range(self.num_levels):
-            v = ctypes.c_int()
+            v, f = ctypes.c_int(), ctypes.c_int()
             self._check(self.lib.stk_tuning(self.h, level, int(dtype), ctypes.byref(v)))
-            out[level] = v.value
+            self._check(self.lib.stk_tuned_smoother(self.h, level, int(dtype), ctypes.byref(f)))
+            out[level] = (v.value, f.value) if with_smoother else v.value
         return out
 
     def coarse_solve(self, b, x):

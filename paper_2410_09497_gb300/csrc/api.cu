@@ -93,6 +93,26 @@ int check_3d(stk_problem* P, const char* what) {
   return STK_OK;
 }
 
+// x[i] = a deterministic value in [-1, 1) (a hash of i and the seed): the
+// autotuner's smoothing input, nonzero so that no local solve stops early
+__global__ void fill_pattern_kernel(void* x, int64_t n, int f32, unsigned seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + seed;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double v = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    if (f32)
+      static_cast<float*>(x)[i] = (float)v;
+    else
+      static_cast<double*>(x)[i] = v;
+  }
+}
+
+void fill_pattern(void* x, int64_t n, int dtype, unsigned seed, cudaStream_t s) {
+  fill_pattern_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1216), 256, 0, s>>>(x, n, dtype == STK_F32, seed);
+}
+
 int check_mg(stk_problem* P) {
   if (P->levels[0].n != 2 && P->levels[0].n != 3)
     return fail(P, STK_ESTATE, "the V-cycle needs a hierarchy that coarsens to 2 or 3 cells per side");
@@ -563,6 +583,24 @@ int stk_autotune(stk_problem* P, int dtype) {
       }
     }
     L.apply_chunk[dtype] = best_chunk;
+    // the smoother's form on the levels that are smoothed (all but the
+    // coarsest): one step of each, on a deterministic nonzero x and b
+    if (e == cudaSuccess && l > 0) {
+      fill_pattern(x, L.ntotal, dtype, 1, P->stream);
+      fill_pattern(y, L.ntotal, dtype, 2, P->stream);
+      e = cudaGetLastError();
+      float tf[2] = {1e30f, 1e30f};
+      for (int form = 0; form < 2 && e == cudaSuccess; ++form) {
+        L.fused_pick[dtype] = form;
+        e = stk::run_smooth(P, (int)l, dtype, x, y);  // warm-up (builds Direct inverses if needed)
+        if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = stk::run_smooth(P, (int)l, dtype, x, y);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&tf[form], e0, e1);
+      }
+      L.fused_pick[dtype] = tf[1] < tf[0] ? 1 : 0;
+    }
     if (x) cudaFree(x);
     if (y) cudaFree(y);
   }
@@ -578,6 +616,13 @@ int stk_autotune(stk_problem* P, int dtype) {
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return status_of(P, e, "autotune");
+}
+
+int stk_tuned_smoother(const stk_problem* P, int level, int dtype, int* fused) {
+  if (!P || !fused || level < 0 || level >= (int)P->levels.size() || (dtype != STK_F64 && dtype != STK_F32))
+    return STK_EINVAL;
+  *fused = P->levels[level].fused_pick[dtype];
+  return STK_OK;
 }
 
 int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_cta) {

@@ -227,8 +227,10 @@ cudaError_t run_smooth(stk_problem* P, int level, int dtype, void* x, const void
   if (e == cudaSuccess && P->opt.local_cg_mode == STK_LOCAL_DIRECT) e = ensure_direct(P, level);
   if (e != cudaSuccess) return e;
   void* r = P->mg[dtype].r[level];
+  const int pick = P->levels[level].fused_pick[dtype];
+  const bool fused = pick >= 0 ? pick == 1 : P->opt.fused_smoother != 0;
   for (int colour = 0; colour < 8; ++colour) {
-    if (P->opt.fused_smoother) {
+    if (fused) {
       void* xin = (colour % 2 == 0) ? x : r;
       void* xout = (colour % 2 == 0) ? r : x;
       e = launch_copy_unowned(P, level, dtype, colour, xin, xout);

@@ -315,3 +315,22 @@ def test_direct_local_solver_solve(stk):
             assert abs(info["iterations"] - info_ref["iterations"]) <= 1
         P.close()
     assert its[stk.LOCAL_DIRECT] <= its[stk.CG_FIXED]
+
+
+def test_autotuned_smoother_keeps_parity(stk):
+    """stk_autotune also picks the smoother's form per smoothed level (split or
+    fused, the faster); the smoothing step it then runs still matches the
+    oracle's."""
+    n, k = 8, 2
+    H = Hierarchy(n, k, local=("schur", 15))
+    d = H.levels[-1].disc
+    x0 = random_vector(1700, d.N) * d.free_mask()
+    b = random_vector(1701, d.N) * d.free_mask()
+    ref = H.smooth(len(H.levels) - 1, x0, b)
+    P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
+    tuned = P.autotune(stk.F64, with_smoother=True)
+    assert tuned[0][1] == -1 and all(tuned[level][1] in (0, 1) for level in range(1, P.num_levels))
+    x = dev(x0.copy())
+    P.smooth(x, dev(b))
+    check(relerr(x.cpu().numpy(), ref), 1e-12)
+    P.close()
