@@ -67,11 +67,14 @@ void free_problem(stk_problem* P) {
     for (auto* v : {&P->mg[d].r, &P->mg[d].b, &P->mg[d].x})
       for (void* p : *v)
         if (p) cudaFree(p);
-  if (P->kry.V) cudaFree(P->kry.V);
-  if (P->kry.Z) cudaFree(P->kry.Z);
-  if (P->kry.partial) cudaFree(P->kry.partial);
-  if (P->kry.h) cudaFree(P->kry.h);
-  if (P->kry.h_host) cudaFreeHost(P->kry.h_host);
+  stk::KrylovWork& K = P->kry;
+  if (K.solve_graph) cudaGraphExecDestroy(K.solve_graph);
+  for (double* d : {K.V, K.Z, K.w, K.zbuf, K.partial, K.h})
+    if (d) cudaFree(d);
+  if (K.state) cudaFree(K.state);
+  if (K.state_host) cudaFreeHost(K.state_host);
+  for (cudaStream_t s : K.side)
+    if (s) cudaStreamDestroy(s);
   if (P->xfer64) cudaFree(P->xfer64);
   if (P->xfer32) cudaFree(P->xfer32);
   if (P->pmean_w) cudaFree(P->pmean_w);
@@ -607,12 +610,12 @@ int stk_autotune(stk_problem* P, int dtype) {
   // a V-cycle graph captured before tuning replays the old launch shapes:
   // drop it so that the next solve captures the tuned ones
   stk::MgWork& W = P->mg[dtype];
-  if (W.graph) {
-    cudaStreamSynchronize(P->stream);
-    cudaGraphExecDestroy(W.graph);
-  }
+  cudaStreamSynchronize(P->stream);
+  if (W.graph) cudaGraphExecDestroy(W.graph);
   W.graph = nullptr;
   W.vcycle_runs = 0;
+  if (P->kry.solve_graph) cudaGraphExecDestroy(P->kry.solve_graph);  // holds the V-cycle's launches too
+  P->kry.solve_graph = nullptr;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return status_of(P, e, "autotune");

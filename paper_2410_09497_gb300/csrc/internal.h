@@ -227,11 +227,19 @@ struct MgWork {
 
 struct KrylovWork {
   bool ready = false;
-  double* V = nullptr;  // (restart + 1) basis vectors
-  double* Z = nullptr;  // restart preconditioned vectors
+  double* V = nullptr;     // (restart + 1) basis vectors
+  double* Z = nullptr;     // restart preconditioned vectors
+  double* w = nullptr;     // the new Arnoldi vector
+  double* zbuf = nullptr;  // FP64 copy of the FP32 V-cycle's output (mixed precision)
   double* partial = nullptr;
-  double* h = nullptr;
-  double* h_host = nullptr;  // pinned
+  double* h = nullptr;     // Gram-Schmidt coefficients and norms
+  void* state = nullptr;       // device state of the FGMRES recurrence (solver.cu)
+  void* state_host = nullptr;  // pinned copy
+  cudaStream_t side[2] = {nullptr, nullptr};  // capture streams of the loop bodies
+  cudaGraphExec_t solve_graph = nullptr;       // the whole solve for (key_b, key_x, key_rtol)
+  const double* key_b = nullptr;
+  double* key_x = nullptr;
+  double key_rtol = 0;
 };
 
 struct Coarse3Factors;  // coarse3.cu

@@ -31,28 +31,20 @@ __global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, i
     dst[i] = (D)src[i];
 }
 
-// partial[b * nv + i] = sum over block b's share of V_i . w   (V_i = V + i * n)
-__global__ void __launch_bounds__(kRedThreads) multidot_kernel(const double* __restrict__ V, int nv,
-                                                                const double* __restrict__ w, int64_t n,
-                                                                double* __restrict__ partial) {
-  __shared__ double red[kRedThreads / 32][kMaxBasis];
-  double acc[kMaxBasis];
-  for (int i = 0; i < nv; ++i) acc[i] = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const double we = w[e];
-    for (int i = 0; i < nv; ++i) acc[i] += V[(int64_t)i * n + e] * we;
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = 0; i < nv; ++i) {
-    double v = acc[i];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wid][i] = v;
-  }
+// partial[b] = block b's share of a . w (one scalar accumulator per thread)
+__global__ void __launch_bounds__(kRedThreads) dot_kernel(const double* __restrict__ a, const double* __restrict__ w,
+                                                          int64_t n, double* __restrict__ partial) {
+  __shared__ double red[kRedThreads / 32];
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    acc += a[e] * w[e];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+  if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int q = 0; q < kRedThreads / 32; ++q) s += red[q][i];
-    partial[(int64_t)blockIdx.x * nv + i] = s;
+    for (int q = 0; q < kRedThreads / 32; ++q) s += red[q];
+    partial[blockIdx.x] = s;
   }
 }
 
@@ -64,40 +56,6 @@ __global__ void finish_dot_kernel(const double* __restrict__ partial, int nblock
   double s = 0.0;
   for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * nv + i];
   out[i] = accumulate ? out[i] + s : s;
-}
-
-// w -= sum_i h[i] V_i
-__global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V, int nv,
-                                  const double* __restrict__ h, int64_t n) {
-  __shared__ double hs[kMaxBasis];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
-  __syncthreads();
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = w[e];
-    for (int i = 0; i < nv; ++i) s -= hs[i] * V[(int64_t)i * n + e];
-    w[e] = s;
-  }
-}
-
-// dst = src / *scale   (scale on the device)
-__global__ void scale_kernel(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ s,
-                             int64_t n) {
-  const double inv = 1.0 / *s;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = src[e] * inv;
-}
-
-struct Coeffs {
-  double y[kMaxBasis];
-};
-
-// x += sum_i y_i Z_i
-__global__ void update_x_kernel(double* __restrict__ x, const double* __restrict__ Z, int nz, Coeffs c, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = x[e];
-    for (int i = 0; i < nz; ++i) s += c.y[i] * Z[(int64_t)i * n + e];
-    x[e] = s;
-  }
 }
 
 // sum_i W_i p_i and sum_i W_i over the pressure block (W = Gauss weight products)
@@ -380,6 +338,225 @@ cudaError_t run_coarse_solve(stk_problem* P, int dtype, const void* b, void* x) 
 }
 
 // -------------------------------------------------------------------- FGMRES
+// Flexible GMRES(restart), right preconditioned by one V-cycle, x0 = 0
+// (Sec. 3.3), with its whole scalar recurrence on the device: the Arnoldi
+// coefficients, the Givens rotations, the least-squares update and the
+// stopping tests live in a GmresState in device memory and are advanced by
+// single-thread kernels, and every kernel that depends on the step j reads it
+// from there.  So the same launch sequence runs two ways: driven by the host,
+// which reads a few flags after each step (no stream, or graphs off), or as
+// one CUDA graph per solve whose two loops are conditional WHILE nodes set by
+// those kernels: a solve is then one graph launch and one read at the end.
+// Both ways run the same kernels in the same order: bitwise the same result.
+
+struct GmresState {
+  // flags the host reads while it drives the loop (first 64 bytes)
+  int j;          // current Arnoldi step of the cycle
+  int its;        // steps so far
+  int jdone;      // steps of the current cycle
+  int stop;       // the cycle ends after this step
+  int converged;  // true residual below rtol ||b||
+  int more;       // another cycle follows
+  int m, max_iter;
+  double bnorm, beta, hn, rtol;
+  double H[(kMaxBasis + 1) * kMaxBasis];  // H[i * kMaxBasis + col]
+  double cs[kMaxBasis], sn[kMaxBasis], g[kMaxBasis + 1], y[kMaxBasis];
+  double res[256];  // relative residual estimate after each step, res[0] = 1
+};
+constexpr size_t kStateFlags = 64;
+
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, unsigned v) {
+  if (use) cudaGraphSetConditional(h, v);
+}
+
+// bnorm = ||b|| from h[0]; start of the first cycle
+__global__ void gm_start_kernel(GmresState* st, const double* __restrict__ h, double rtol, int m, int max_iter,
+                                cudaGraphConditionalHandle hout, int use) {
+  st->m = m;
+  st->max_iter = max_iter;
+  st->rtol = rtol;
+  st->bnorm = sqrt(h[0]);
+  st->beta = st->bnorm;
+  st->its = 0;
+  st->j = 0;
+  st->jdone = 0;
+  st->stop = 0;
+  st->converged = st->bnorm == 0.0;
+  st->more = !st->converged;
+  st->res[0] = 1.0;
+  set_cond(hout, use, st->more ? 1u : 0u);
+}
+
+// dst = src / beta (V_0 of a cycle); nothing when no cycle follows
+__global__ void gm_scale_kernel(const double* __restrict__ src, double* __restrict__ dst, const GmresState* st,
+                                int64_t n) {
+  if (!st->more) return;
+  const double inv = 1.0 / st->beta;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e] * inv;
+}
+
+__global__ void gm_cycle_begin_kernel(GmresState* st, cudaGraphConditionalHandle hin, int use) {
+  st->j = 0;
+  st->stop = 0;
+  for (int i = 0; i < (kMaxBasis + 1) * kMaxBasis; ++i) st->H[i] = 0.0;
+  for (int i = 0; i <= kMaxBasis; ++i) st->g[i] = 0.0;
+  st->g[0] = st->beta;
+  set_cond(hin, use, 1u);
+}
+
+// dst = (T) V_j
+template <typename T>
+__global__ void gm_copy_in_kernel(const double* __restrict__ V, const GmresState* st, int64_t n, T* __restrict__ dst) {
+  const double* v = V + (int64_t)st->j * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (T)v[e];
+}
+
+// Z_j = z (and zbuf = z, the apply's fixed input, when z is FP32)
+template <typename T>
+__global__ void gm_copy_out_kernel(const T* __restrict__ z, double* __restrict__ Z, const GmresState* st, int64_t n,
+                                   double* __restrict__ zbuf) {
+  double* zj = Z + (int64_t)st->j * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)z[e];
+    zj[e] = v;
+    if (zbuf) zbuf[e] = v;
+  }
+}
+
+// partial[b * nv + i] = block b's share of V_i . w, i <= j (nv = j + 1 from the state)
+__global__ void __launch_bounds__(kRedThreads) gm_multidot_kernel(const double* __restrict__ V, const GmresState* st,
+                                                                   const double* __restrict__ w, int64_t n,
+                                                                   double* __restrict__ partial) {
+  __shared__ double red[kRedThreads / 32][kMaxBasis];
+  const int nv = st->j + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // the basis vectors in chunks of 8 accumulators per thread (registers, no local array)
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+      const double we = w[e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u < nv) acc[u] += V[(int64_t)(i0 + u) * n + e] * we;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      double v = acc[u];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && i0 + u < nv) red[wid][i0 + u] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) s += red[q][i];
+    partial[(int64_t)blockIdx.x * kMaxBasis + i] = s;
+  }
+}
+
+// out[i] = sum over blocks, fixed order (deterministic); nv = j + 1, or 1 when `one`
+__global__ void gm_finish_dot_kernel(const double* __restrict__ partial, int nblocks, const GmresState* st, int one,
+                                     double* __restrict__ out) {
+  const int nv = one ? 1 : st->j + 1;
+  const int i = threadIdx.x;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * kMaxBasis + i];
+  out[i] = s;
+}
+
+// w -= sum_{i <= j} h[i] V_i
+__global__ void gm_axpy_kernel(double* __restrict__ w, const double* __restrict__ V, const GmresState* st,
+                               const double* __restrict__ h, int64_t n) {
+  __shared__ double hs[kMaxBasis];
+  const int nv = st->j + 1;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[e];
+    for (int i = 0; i < nv; ++i) s -= hs[i] * V[(int64_t)i * n + e];
+    w[e] = s;
+  }
+}
+
+// one Arnoldi step on the device: column j of H from the two Gram-Schmidt
+// passes (h[i] + h[kMaxBasis + i]) and the norm (h[2 kMaxBasis]), the earlier
+// Givens rotations, a new one, the residual estimate and the stopping test
+__global__ void gm_arnoldi_kernel(GmresState* st, const double* __restrict__ h, cudaGraphConditionalHandle hin,
+                                  int use) {
+  const int j = st->j, m = st->m;
+  double* H = st->H;
+  for (int i = 0; i <= j; ++i) H[i * kMaxBasis + j] = h[i] + h[kMaxBasis + i];
+  const double hn = sqrt(h[2 * kMaxBasis]);
+  H[(j + 1) * kMaxBasis + j] = hn;
+  st->hn = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = st->cs[i] * H[i * kMaxBasis + j] + st->sn[i] * H[(i + 1) * kMaxBasis + j];
+    H[(i + 1) * kMaxBasis + j] = -st->sn[i] * H[i * kMaxBasis + j] + st->cs[i] * H[(i + 1) * kMaxBasis + j];
+    H[i * kMaxBasis + j] = t;
+  }
+  const double den = hypot(H[j * kMaxBasis + j], H[(j + 1) * kMaxBasis + j]);
+  st->cs[j] = H[j * kMaxBasis + j] / den;
+  st->sn[j] = H[(j + 1) * kMaxBasis + j] / den;
+  H[j * kMaxBasis + j] = den;
+  H[(j + 1) * kMaxBasis + j] = 0.0;
+  st->g[j + 1] = -st->sn[j] * st->g[j];
+  st->g[j] = st->cs[j] * st->g[j];
+  st->its += 1;
+  st->jdone = j + 1;
+  if (st->its < 256) st->res[st->its] = fabs(st->g[j + 1]) / st->bnorm;
+  const int stop = fabs(st->g[j + 1]) <= st->rtol * st->bnorm || st->its >= st->max_iter || j + 1 == m;
+  st->stop = stop;
+  if (!stop) st->j = j + 1;
+  set_cond(hin, use, stop ? 0u : 1u);
+}
+
+// V_{jdone} = w / hn (the next basis vector; harmless when the cycle stops)
+__global__ void gm_normalize_kernel(double* __restrict__ V, const double* __restrict__ w, const GmresState* st,
+                                    int64_t n) {
+  double* v = V + (int64_t)st->jdone * n;
+  const double inv = 1.0 / st->hn;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    v[e] = w[e] * inv;
+}
+
+// y = H^{-1} g on the cycle's jdone steps (upper triangular)
+__global__ void gm_solve_y_kernel(GmresState* st) {
+  const int jd = st->jdone;
+  for (int i = jd - 1; i >= 0; --i) {
+    double s = st->g[i];
+    for (int l = i + 1; l < jd; ++l) s -= st->H[i * kMaxBasis + l] * st->y[l];
+    st->y[i] = s / st->H[i * kMaxBasis + i];
+  }
+}
+
+// x += sum_{i < jdone} y_i Z_i
+__global__ void gm_update_x_kernel(double* __restrict__ x, const double* __restrict__ Z, const GmresState* st,
+                                   int64_t n) {
+  __shared__ double ys[kMaxBasis];
+  const int jd = st->jdone;
+  for (int i = threadIdx.x; i < jd; i += blockDim.x) ys[i] = st->y[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = x[e];
+    for (int i = 0; i < jd; ++i) s += ys[i] * Z[(int64_t)i * n + e];
+    x[e] = s;
+  }
+}
+
+// the true residual's norm (h[0]) decides: converged, or another cycle
+__global__ void gm_restart_kernel(GmresState* st, const double* __restrict__ h, cudaGraphConditionalHandle hout,
+                                  int use) {
+  st->beta = sqrt(h[0]);
+  st->converged = st->beta <= st->rtol * st->bnorm;
+  st->more = !st->converged && st->its < st->max_iter;
+  set_cond(hout, use, st->more ? 1u : 0u);
+}
+
 cudaError_t ensure_krylov(stk_problem* P) {
   KrylovWork& K = P->kry;
   const int m = P->opt.gmres_restart;
@@ -387,27 +564,32 @@ cudaError_t ensure_krylov(stk_problem* P) {
   const int64_t n = P->levels.back().ntotal;
   cudaError_t e = dev_alloc(&K.V, sizeof(double) * (size_t)(m + 1) * n);
   if (e == cudaSuccess) e = dev_alloc(&K.Z, sizeof(double) * (size_t)m * n);
+  if (e == cudaSuccess) e = dev_alloc(&K.w, sizeof(double) * (size_t)n);
+  if (e == cudaSuccess && P->opt.precision == STK_PREC_MIXED) e = dev_alloc(&K.zbuf, sizeof(double) * (size_t)n);
   if (e == cudaSuccess) e = dev_alloc(&K.partial, sizeof(double) * (size_t)kRedBlocks * kMaxBasis);
-  if (e == cudaSuccess) e = dev_alloc(&K.h, sizeof(double) * 2 * kMaxBasis);
-  if (e == cudaSuccess) e = host_alloc_pinned(&K.h_host, sizeof(double) * 2 * kMaxBasis);
+  if (e == cudaSuccess) e = dev_alloc(&K.h, sizeof(double) * (2 * kMaxBasis + 2));
+  if (e == cudaSuccess) e = dev_alloc(&K.state, sizeof(GmresState));
+  if (e == cudaSuccess) e = host_alloc_pinned(&K.state_host, sizeof(GmresState));
   if (e != cudaSuccess) {  // leave nothing half allocated
-    for (double** d : {&K.V, &K.Z, &K.partial, &K.h})
+    for (double** d : {&K.V, &K.Z, &K.w, &K.zbuf, &K.partial, &K.h})
       if (*d) {
         cudaFree(*d);
         *d = nullptr;
       }
-    if (K.h_host) cudaFreeHost(K.h_host);
-    K.h_host = nullptr;
+    if (K.state) cudaFree(K.state);
+    K.state = nullptr;
+    if (K.state_host) cudaFreeHost(K.state_host);
+    K.state_host = nullptr;
     return e;
   }
   K.ready = true;
   return cudaSuccess;
 }
 
-static cudaError_t dots(stk_problem* P, const double* V, int nv, const double* w, int64_t n, double* out,
-                        int accumulate) {
-  multidot_kernel<<<kRedBlocks, kRedThreads, 0, P->stream>>>(V, nv, w, n, P->kry.partial);
-  finish_dot_kernel<<<1, kMaxBasis, 0, P->stream>>>(P->kry.partial, kRedBlocks, nv, out, accumulate);
+// *out = a . w (deterministic two-stage reduction)
+static cudaError_t dot(stk_problem* P, const double* a, const double* w, int64_t n, double* out) {
+  dot_kernel<<<kRedBlocks, kRedThreads, 0, P->stream>>>(a, w, n, P->kry.partial);
+  finish_dot_kernel<<<1, 32, 0, P->stream>>>(P->kry.partial, kRedBlocks, 1, out, 0);
   return cudaGetLastError();
 }
 
@@ -440,24 +622,6 @@ static cudaError_t fixed_vcycle(stk_problem* P, int dtype) {
   return cudaGraphLaunch(W.graph, P->stream);
 }
 
-static cudaError_t precondition(stk_problem* P, const double* v, double* z) {
-  const int L = (int)P->levels.size() - 1;
-  const int64_t n = P->levels[L].ntotal;
-  if (P->opt.precision == STK_PREC_MIXED) {
-    MgWork& W = P->mg[STK_F32];
-    convert_kernel<double, float><<<grid_for(n), 256, 0, P->stream>>>(v, (float*)W.b[L], n);
-    cudaError_t e = fixed_vcycle(P, STK_F32);
-    if (e != cudaSuccess) return e;
-    convert_kernel<float, double><<<grid_for(n), 256, 0, P->stream>>>((const float*)W.x[L], z, n);
-    return cudaGetLastError();
-  }
-  MgWork& W = P->mg[STK_F64];
-  cudaError_t e = cudaMemcpyAsync(W.b[L], v, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream);
-  if (e == cudaSuccess) e = fixed_vcycle(P, STK_F64);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(z, W.x[L], sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream);
-  return e;
-}
-
 cudaError_t project_pressure_mean(stk_problem* P, double* x) {
   if (P->dim == 2) return launch_pressure_mean_planar(P, x, P->kry.partial, kRedBlocks);
   const Level& L = P->levels.back();
@@ -467,264 +631,297 @@ cudaError_t project_pressure_mean(stk_problem* P, double* x) {
   return cudaGetLastError();
 }
 
-// dst = src * s (host scalar)
-__global__ void scale_by_kernel(const double* __restrict__ src, double* __restrict__ dst, double s, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = src[e] * s;
+// --- the launch sequence of the solve, shared by both drivers.  `use` 1:
+// the kernels set the conditional handles (graph); 0: the host drives.
+static int mixed(const stk_problem* P) { return P->opt.precision == STK_PREC_MIXED; }
+
+static cudaError_t issue_start(stk_problem* P, const double* b, double* x, double rtol, cudaGraphConditionalHandle hout,
+                               int use) {
+  KrylovWork& K = P->kry;
+  const int64_t N = P->levels.back().ntotal;
+  GmresState* st = static_cast<GmresState*>(K.state);
+  cudaError_t e = dot(P, b, b, N, K.h);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(double) * N, P->stream);
+  if (e != cudaSuccess) return e;
+  gm_start_kernel<<<1, 1, 0, P->stream>>>(st, K.h, rtol, P->opt.gmres_restart, P->opt.max_iter, hout, use);
+  gm_scale_kernel<<<grid_for(N), 256, 0, P->stream>>>(b, K.V, st, N);
+  return cudaGetLastError();
 }
 
-// Flexible GMRES(restart) as a resumable state machine: issue() enqueues the
-// GPU work of the current phase on the problem's stream and ends with a copy
-// of the scalars the host needs; complete() runs after the stream is idle and
-// decides the next phase.  stk_solve drives one machine; stk_solve_batch
-// interleaves many, one stream each, so their kernels overlap on the GPU.
-struct SolveMachine {
-  enum Phase { START, ITER, CYCLE_END, FINISH, DONE };
-  stk_problem* P = nullptr;
-  const double* b = nullptr;
-  double* x = nullptr;
-  double rtol = 0;
-  stk_solve_info* info = nullptr;
+// one Arnoldi step: z = M^{-1} V_j (the V-cycle inline, or its own graph when
+// `vcycle_graph`), w = A z, two Gram-Schmidt passes, the norm, the device
+// step and V_{j+1}
+static cudaError_t issue_iter(stk_problem* P, cudaGraphConditionalHandle hin, int use, bool vcycle_graph) {
+  KrylovWork& K = P->kry;
+  const int L = (int)P->levels.size() - 1;
+  const int64_t N = P->levels[L].ntotal;
+  GmresState* st = static_cast<GmresState*>(K.state);
+  const int dt = mixed(P) ? STK_F32 : STK_F64;
+  MgWork& W = P->mg[dt];
+  cudaError_t e = cudaSuccess;
+  if (dt == STK_F32)
+    gm_copy_in_kernel<float><<<grid_for(N), 256, 0, P->stream>>>(K.V, st, N, (float*)W.b[L]);
+  else
+    gm_copy_in_kernel<double><<<grid_for(N), 256, 0, P->stream>>>(K.V, st, N, (double*)W.b[L]);
+  e = vcycle_graph ? fixed_vcycle(P, dt) : vcycle_rec(P, L, dt, W.b[L], W.x[L]);
+  if (e != cudaSuccess) return e;
+  const double* z = nullptr;
+  if (dt == STK_F32) {
+    gm_copy_out_kernel<float><<<grid_for(N), 256, 0, P->stream>>>((const float*)W.x[L], K.Z, st, N, K.zbuf);
+    z = K.zbuf;
+  } else {
+    gm_copy_out_kernel<double><<<grid_for(N), 256, 0, P->stream>>>((const double*)W.x[L], K.Z, st, N, nullptr);
+    z = (const double*)W.x[L];
+  }
+  e = launch_apply(P, L, STK_F64, z, nullptr, K.w, 1.0);
+  if (e != cudaSuccess) return e;
+  for (int pass = 0; pass < 2; ++pass) {
+    double* hp = K.h + pass * kMaxBasis;
+    gm_multidot_kernel<<<kRedBlocks, kRedThreads, 0, P->stream>>>(K.V, st, K.w, N, K.partial);
+    gm_finish_dot_kernel<<<1, kMaxBasis, 0, P->stream>>>(K.partial, kRedBlocks, st, 0, hp);
+    gm_axpy_kernel<<<grid_for(N), 256, 0, P->stream>>>(K.w, K.V, st, hp, N);
+  }
+  e = dot(P, K.w, K.w, N, K.h + 2 * kMaxBasis);
+  if (e != cudaSuccess) return e;
+  gm_arnoldi_kernel<<<1, 1, 0, P->stream>>>(st, K.h, hin, use);
+  gm_normalize_kernel<<<grid_for(N), 256, 0, P->stream>>>(K.V, K.w, st, N);
+  return cudaGetLastError();
+}
+
+// end of a cycle: x += Z y, the true residual into V_m and its norm, the
+// restart decision and V_0 of the next cycle
+static cudaError_t issue_cycle_end(stk_problem* P, const double* b, double* x, cudaGraphConditionalHandle hout,
+                                   int use) {
+  KrylovWork& K = P->kry;
+  const int L = (int)P->levels.size() - 1;
+  const int64_t N = P->levels[L].ntotal;
+  GmresState* st = static_cast<GmresState*>(K.state);
+  double* rtmp = K.V + (size_t)P->opt.gmres_restart * N;
+  gm_solve_y_kernel<<<1, 1, 0, P->stream>>>(st);
+  gm_update_x_kernel<<<grid_for(N), 256, 0, P->stream>>>(x, K.Z, st, N);
+  cudaError_t e = launch_apply(P, L, STK_F64, x, b, rtmp, -1.0);
+  if (e == cudaSuccess) e = dot(P, rtmp, rtmp, N, K.h);
+  if (e != cudaSuccess) return e;
+  gm_restart_kernel<<<1, 1, 0, P->stream>>>(st, K.h, hout, use);
+  gm_scale_kernel<<<grid_for(N), 256, 0, P->stream>>>(rtmp, K.V, st, N);
+  return cudaGetLastError();
+}
+
+static cudaError_t read_state(stk_problem* P, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(P->kry.state_host, P->kry.state, bytes, cudaMemcpyDeviceToHost, P->stream);
+  return e == cudaSuccess ? cudaStreamSynchronize(P->stream) : e;
+}
+
+// Everything a solve needs, set up before any capture: the Krylov basis, the
+// multigrid workspace, the coarse solver, the Direct inverses and the kernel
+// attributes (one V-cycle and one FP64 apply run directly the first time).
+static cudaError_t prepare_solve(stk_problem* P) {
+  cudaError_t e = ensure_krylov(P);
+  const int dt = mixed(P) ? STK_F32 : STK_F64;
+  if (e == cudaSuccess) e = ensure_mg_workspace(P, dt);
+  if (e == cudaSuccess) e = ensure_coarse(P);
+  if (e != cudaSuccess) return e;
+  MgWork& W = P->mg[dt];
+  if (W.vcycle_runs == 0) {
+    const int L = (int)P->levels.size() - 1;
+    const size_t es = dt == STK_F64 ? 8 : 4;
+    e = cudaMemsetAsync(W.b[L], 0, (size_t)P->levels[L].ntotal * es, P->stream);
+    if (e == cudaSuccess) e = fixed_vcycle(P, dt);
+    // both forms of the FP64 apply (kernel attributes are set outside any capture)
+    if (e == cudaSuccess) e = launch_apply(P, L, STK_F64, P->kry.w, nullptr, P->kry.V, 1.0);
+    if (e == cudaSuccess) e = launch_apply(P, L, STK_F64, P->kry.w, P->kry.V, P->kry.Z, -1.0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  }
+  return e;
+}
+
+// The whole solve as one graph: start, WHILE (another cycle) { cycle begin,
+// WHILE (another step) { Arnoldi step }, cycle end }, pressure mean, state
+// to the host.  The loop bodies are captured on two side streams into the
+// conditional nodes' graphs; the loop conditions are set by the kernels before
+// each test (gm_start / gm_restart for the outer loop, gm_cycle_begin /
+// gm_arnoldi for the inner one).
+static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle* h, cudaGraph_t* body, bool create_handle) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t r = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (r == cudaSuccess && create_handle) r = cudaGraphConditionalHandleCreate(h, g, 0, 0);
+  if (r != cudaSuccess) return r;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = *h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  r = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+  if (r != cudaSuccess) return r;
+  *body = cp.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+static cudaError_t build_solve_graph(stk_problem* P, const double* b, double* x, double rtol) {
+  KrylovWork& K = P->kry;
+  for (int i = 0; i < 2; ++i)
+    if (!K.side[i]) {
+      cudaError_t e = cudaStreamCreateWithFlags(&K.side[i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+  const cudaStream_t main = P->stream;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaError_t e = cudaStreamBeginCapture(main, mode);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = cudaSuccess;
+  cudaGraphConditionalHandle hout = 0, hin = 0;
+  cudaGraph_t top = nullptr, outer = nullptr, inner = nullptr;
+  {
+    cudaStreamCaptureStatus cs;
+    e1 = cudaStreamGetCaptureInfo(main, &cs, nullptr, &top, nullptr, nullptr, nullptr);
+    if (e1 == cudaSuccess) e1 = cudaGraphConditionalHandleCreate(&hout, top, 0, 0);
+  }
+  if (e1 == cudaSuccess) e1 = issue_start(P, b, x, rtol, hout, 1);
+  if (e1 == cudaSuccess) e1 = add_while(main, &hout, &outer, false);
+  if (e1 == cudaSuccess) {
+    // outer body on side stream 0
+    e1 = cudaStreamBeginCaptureToGraph(K.side[0], outer, nullptr, nullptr, 0, mode);
+    if (e1 == cudaSuccess) {
+      P->stream = K.side[0];
+      cudaError_t eb = cudaGraphConditionalHandleCreate(&hin, outer, 0, 0);
+      if (eb == cudaSuccess) {
+        gm_cycle_begin_kernel<<<1, 1, 0, P->stream>>>(static_cast<GmresState*>(K.state), hin, 1);
+        eb = cudaGetLastError();
+      }
+      if (eb == cudaSuccess) eb = add_while(K.side[0], &hin, &inner, false);
+      if (eb == cudaSuccess) {
+        // inner body on side stream 1: one Arnoldi step with the V-cycle inline
+        eb = cudaStreamBeginCaptureToGraph(K.side[1], inner, nullptr, nullptr, 0, mode);
+        if (eb == cudaSuccess) {
+          P->stream = K.side[1];
+          cudaError_t ei = issue_iter(P, hin, 1, false);
+          cudaGraph_t got = nullptr;
+          eb = cudaStreamEndCapture(K.side[1], &got);
+          if (ei != cudaSuccess) eb = ei;
+          P->stream = K.side[0];
+        }
+      }
+      if (eb == cudaSuccess) eb = issue_cycle_end(P, b, x, hout, 1);
+      cudaGraph_t got = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(K.side[0], &got);
+      e1 = eb != cudaSuccess ? eb : ee;
+      P->stream = main;
+    }
+  }
+  if (e1 == cudaSuccess) e1 = project_pressure_mean(P, x);
+  if (e1 == cudaSuccess)
+    e1 = cudaMemcpyAsync(K.state_host, K.state, sizeof(GmresState), cudaMemcpyDeviceToHost, main);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(main, &graph);
+  P->stream = main;
+  if (e1 != cudaSuccess) e = e1;
+  if (e == cudaSuccess) {
+    if (K.solve_graph) cudaGraphExecDestroy(K.solve_graph);
+    K.solve_graph = nullptr;
+    e = cudaGraphInstantiate(&K.solve_graph, graph, 0);
+    if (e != cudaSuccess) K.solve_graph = nullptr;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (e == cudaSuccess) {
+    K.key_b = b;
+    K.key_x = x;
+    K.key_rtol = rtol;
+  }
+  return e;
+}
+
+static bool use_solve_graph(const stk_problem* P) { return P->opt.use_graphs && P->stream != nullptr; }
+
+// Start a solve: the graph is (re)built for new b, x or rtol and launched;
+// without graphs the host drives the same launches, reading the state's flags
+// after each step.  Returns after the GPU work is enqueued (graph) or done.
+static cudaError_t solve_launch(stk_problem* P, const double* b, double* x, double rtol) {
+  cudaError_t e = prepare_solve(P);
+  if (e != cudaSuccess) return e;
+  KrylovWork& K = P->kry;
+  if (use_solve_graph(P)) {
+    if (!K.solve_graph || K.key_b != b || K.key_x != x || K.key_rtol != rtol) e = build_solve_graph(P, b, x, rtol);
+    if (e == cudaSuccess) e = cudaGraphLaunch(K.solve_graph, P->stream);
+    return e;
+  }
+  GmresState* st = static_cast<GmresState*>(K.state);
+  const GmresState* sh = static_cast<const GmresState*>(K.state_host);
+  e = issue_start(P, b, x, rtol, 0, 0);
+  if (e == cudaSuccess) e = read_state(P, kStateFlags);
+  while (e == cudaSuccess && sh->more) {
+    gm_cycle_begin_kernel<<<1, 1, 0, P->stream>>>(st, 0, 0);
+    do {
+      e = issue_iter(P, 0, 0, true);
+      if (e == cudaSuccess) e = read_state(P, kStateFlags);
+    } while (e == cudaSuccess && !sh->stop);
+    if (e == cudaSuccess) e = issue_cycle_end(P, b, x, 0, 0);
+    if (e == cudaSuccess) e = read_state(P, kStateFlags);
+  }
+  if (e == cudaSuccess) e = project_pressure_mean(P, x);
+  if (e == cudaSuccess) e = read_state(P, sizeof(GmresState));
+  return e;
+}
+
+// After the stream has finished: the info from the state copied to the host.
+static int solve_finish(stk_problem* P, double t0_seconds, stk_solve_info* info, std::string& err) {
+  const GmresState* sh = static_cast<const GmresState*>(P->kry.state_host);
   stk_solve_info local{};
-  Phase phase = START;
-  int status = STK_OK;
-  std::string err;
-  double bnorm = 0, beta = 0, hn_prev = 1.0;
-  int its = 0, j = 0, jdone = 0;
-  bool converged = false, need_normalize = false;
-  std::vector<double> H, cs, sn, g;
-  std::chrono::steady_clock::time_point t0;
-
-  stk_solve_info& I() { return info ? *info : local; }
-  int m() const { return P->opt.gmres_restart; }
-  int64_t n() const { return P->levels.back().ntotal; }
-  cudaStream_t s() const { return P->stream; }
-
-  int prepare() {
-    t0 = std::chrono::steady_clock::now();
-    cudaError_t e = ensure_krylov(P);
-    if (e == cudaSuccess) e = ensure_mg_workspace(P, P->opt.precision == STK_PREC_MIXED ? STK_F32 : STK_F64);
-    if (e == cudaSuccess) e = ensure_coarse(P);
-    if (e != cudaSuccess) return fail_cuda(e, "solve setup");
-    std::memset(&I(), 0, sizeof(stk_solve_info));
-    I().residuals[0] = 1.0;
-    H.assign((m() + 1) * m(), 0.0);
-    cs.assign(m(), 0.0);
-    sn.assign(m(), 0.0);
-    g.assign(m() + 1, 0.0);
-    return STK_OK;
+  stk_solve_info& I = info ? *info : local;
+  std::memset(&I, 0, sizeof(stk_solve_info));
+  I.iterations = sh->its;
+  I.converged = sh->converged ? 1 : 0;
+  I.relres = sh->bnorm > 0 ? sh->beta / sh->bnorm : 0.0;
+  const int nres = std::min(sh->its, 255);
+  for (int i = 0; i <= nres; ++i) I.residuals[i] = sh->res[i];
+  I.residuals[0] = 1.0;
+  const double last = sh->its > 0 && sh->its < 256 ? sh->res[sh->its] : I.relres;
+  I.nu = (sh->its > 0 && last > 0) ? -8.0 / std::log10(std::pow(last, 1.0 / sh->its)) : 0.0;
+  I.seconds = t0_seconds;
+  if (!sh->converged) {
+    err = "GMRES reached max_iter before the tolerance";
+    return STK_ENOCONV;
   }
+  return STK_OK;
+}
 
-  int fail_cuda(cudaError_t e, const char* what) {
-    err = std::string(what) + ": " + cudaGetErrorString(e);
-    status = e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA;
-    phase = DONE;
-    return status;
-  }
-
-  // enqueue the work of the current phase
-  int issue() {
-    KrylovWork& K = P->kry;
-    const int64_t N = n();
-    cudaError_t e = cudaSuccess;
-    switch (phase) {
-      case START:
-        e = dots(P, b, 1, b, N, K.h, 0);
-        if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(double) * N, s());
-        break;
-      case ITER: {
-        double* Vj = K.V + (size_t)j * N;
-        double* Zj = K.Z + (size_t)j * N;
-        double* w = K.V + (size_t)(j + 1) * N;
-        if (j == 0) {
-          // V_0 = r / beta (r = b when x0 = 0, else the last true residual in V_m)
-          const double* r = (its == 0) ? b : K.V + (size_t)m() * N;
-          scale_by_kernel<<<grid_for(N), 256, 0, s()>>>(r, K.V, 1.0 / beta, N);
-        } else if (need_normalize) {
-          scale_by_kernel<<<grid_for(N), 256, 0, s()>>>(Vj, Vj, 1.0 / hn_prev, N);
-        }
-        e = precondition(P, Vj, Zj);
-        if (e == cudaSuccess) e = launch_apply(P, (int)P->levels.size() - 1, STK_F64, Zj, nullptr, w, 1.0);
-        if (e != cudaSuccess) break;
-        // two passes of classical Gram-Schmidt
-        dots(P, K.V, j + 1, w, N, K.h, 0);
-        multi_axpy_kernel<<<grid_for(N), 256, 0, s()>>>(w, K.V, j + 1, K.h, N);
-        dots(P, K.V, j + 1, w, N, K.h + kMaxBasis, 0);
-        multi_axpy_kernel<<<grid_for(N), 256, 0, s()>>>(w, K.V, j + 1, K.h + kMaxBasis, N);
-        e = dots(P, w, 1, w, N, K.h + kMaxBasis + j + 1, 0);
-        break;
-      }
-      case CYCLE_END: {
-        // y = H^{-1} g (upper triangular), x += Z y, true residual into V_m
-        Coeffs c{};
-        const int mm = m();
-        for (int i = jdone - 1; i >= 0; --i) {
-          double sum = g[i];
-          for (int l = i + 1; l < jdone; ++l) sum -= H[i * mm + l] * c.y[l];
-          c.y[i] = sum / H[i * mm + i];
-        }
-        update_x_kernel<<<grid_for(N), 256, 0, s()>>>(x, K.Z, jdone, c, N);
-        double* rtmp = K.V + (size_t)mm * N;
-        e = launch_apply(P, (int)P->levels.size() - 1, STK_F64, x, b, rtmp, -1.0);
-        if (e == cudaSuccess) e = dots(P, rtmp, 1, rtmp, N, K.h, 0);
-        break;
-      }
-      case FINISH:
-        e = project_pressure_mean(P, x);
-        break;
-      case DONE:
-        return status;
-    }
-    if (e == cudaSuccess && phase != FINISH)
-      e = cudaMemcpyAsync(K.h_host, K.h, sizeof(double) * 2 * kMaxBasis, cudaMemcpyDeviceToHost, s());
-    if (e != cudaSuccess) return fail_cuda(e, "solve");
-    return STK_OK;
-  }
-
-  // host side of the current phase, after the stream has finished
-  void complete() {
-    KrylovWork& K = P->kry;
-    const int mm = m();
-    switch (phase) {
-      case START:
-        bnorm = std::sqrt(K.h_host[0]);
-        beta = bnorm;
-        converged = bnorm == 0.0;
-        j = 0;
-        phase = converged ? FINISH : ITER;
-        break;
-      case ITER: {
-        for (int i = 0; i <= j; ++i) H[i * mm + j] = K.h_host[i] + K.h_host[kMaxBasis + i];
-        const double hn = std::sqrt(K.h_host[kMaxBasis + j + 1]);
-        H[(j + 1) * mm + j] = hn;
-        hn_prev = hn;
-        need_normalize = true;
-        if (j == 0) std::fill(g.begin(), g.end(), 0.0), g[0] = beta;
-        for (int i = 0; i < j; ++i) {
-          const double t = cs[i] * H[i * mm + j] + sn[i] * H[(i + 1) * mm + j];
-          H[(i + 1) * mm + j] = -sn[i] * H[i * mm + j] + cs[i] * H[(i + 1) * mm + j];
-          H[i * mm + j] = t;
-        }
-        const double den = std::hypot(H[j * mm + j], H[(j + 1) * mm + j]);
-        cs[j] = H[j * mm + j] / den;
-        sn[j] = H[(j + 1) * mm + j] / den;
-        H[j * mm + j] = den;
-        H[(j + 1) * mm + j] = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        ++its;
-        jdone = j + 1;
-        if (its < 256) I().residuals[its] = std::fabs(g[j + 1]) / bnorm;
-        if (std::fabs(g[j + 1]) <= rtol * bnorm || its >= P->opt.max_iter || j + 1 == mm)
-          phase = CYCLE_END;
-        else
-          ++j;
-        break;
-      }
-      case CYCLE_END:
-        beta = std::sqrt(K.h_host[0]);
-        converged = beta <= rtol * bnorm;
-        if (converged || its >= P->opt.max_iter) {
-          phase = FINISH;
-        } else {
-          j = 0;
-          need_normalize = false;
-          std::fill(H.begin(), H.end(), 0.0);
-          phase = ITER;
-        }
-        break;
-      case FINISH: {
-        stk_solve_info& In = I();
-        In.iterations = its;
-        In.converged = converged ? 1 : 0;
-        In.relres = bnorm > 0 ? beta / bnorm : 0.0;
-        const double last = its > 0 && its < 256 ? In.residuals[its] : In.relres;
-        In.nu = (its > 0 && last > 0) ? -8.0 / std::log10(std::pow(last, 1.0 / its)) : 0.0;
-        In.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (!converged) {
-          err = "GMRES reached max_iter before the tolerance";
-          status = STK_ENOCONV;
-        }
-        phase = DONE;
-        break;
-      }
-      case DONE:
-        break;
-    }
-  }
-};
+static int cuda_status(cudaError_t e, const char* what, std::string& err) {
+  err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA;
+}
 
 int run_solve(stk_problem* P, const double* b, double* x, double rtol, stk_solve_info* info, std::string& err) {
-  SolveMachine M;
-  M.P = P;
-  M.b = b;
-  M.x = x;
-  M.rtol = rtol;
-  M.info = info;
-  if (M.prepare() != STK_OK) {
-    err = M.err;
-    return M.status;
-  }
-  while (M.phase != SolveMachine::DONE) {
-    if (M.issue() != STK_OK) break;
-    cudaError_t e = cudaStreamSynchronize(P->stream);
-    if (e != cudaSuccess) {
-      M.fail_cuda(e, "solve");
-      break;
-    }
-    M.complete();
-  }
-  err = M.err;
-  return M.status;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaError_t e = solve_launch(P, b, x, rtol);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) return cuda_status(e, "solve", err);
+  return solve_finish(P, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), info, err);
 }
 
+// Many problems: every solve is launched (as one graph on the problem's own
+// stream where it has one: the solves then run concurrently, with no host
+// work between their steps), then all streams are waited for.
 int run_solve_batch(stk_problem* const* Ps, int count, const double* const* b, double* const* x, double rtol,
                     stk_solve_info* infos, std::string& err) {
-  std::vector<SolveMachine> M(count);
-  for (int i = 0; i < count; ++i) {
-    M[i].P = Ps[i];
-    M[i].b = b[i];
-    M[i].x = x[i];
-    M[i].rtol = rtol;
-    M[i].info = infos ? &infos[i] : nullptr;
-    if (M[i].prepare() != STK_OK) {
-      err = "problem " + std::to_string(i) + ": " + M[i].err;
-      return M[i].status;
-    }
-  }
-  // Each solve advances on its own: whenever its stream has drained, its
-  // phase is completed on the host and the next one issued at once, so a
-  // short phase of a small problem never waits for a long phase of a large
-  // one.  The loop polls the streams (cudaStreamQuery) until all are done.
-  int active = 0;
-  for (auto& m : M) {
-    m.issue();
-    if (m.phase != SolveMachine::DONE) ++active;
-  }
-  while (active > 0) {
-    bool progressed = false;
-    for (int i = 0; i < count; ++i) {
-      SolveMachine& m = M[i];
-      if (m.phase == SolveMachine::DONE) continue;
-      const cudaError_t q = cudaStreamQuery(m.s());
-      if (q == cudaErrorNotReady) continue;
-      progressed = true;
-      if (q != cudaSuccess) {
-        m.fail_cuda(q, "solve");
-      } else {
-        m.complete();
-        if (m.phase != SolveMachine::DONE) m.issue();
-      }
-      if (m.phase == SolveMachine::DONE) --active;
-    }
-    if (!progressed) std::this_thread::yield();
-  }
-  int worst = STK_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<cudaError_t> status(count, cudaSuccess);
+  for (int i = 0; i < count; ++i) status[i] = solve_launch(Ps[i], b[i], x[i], rtol);
   for (int i = 0; i < count; ++i)
-    if (M[i].status != STK_OK && (worst == STK_OK || M[i].status != STK_ENOCONV)) {
-      worst = M[i].status;
-      err = "problem " + std::to_string(i) + ": " + M[i].err;
+    if (status[i] == cudaSuccess) status[i] = cudaStreamSynchronize(Ps[i]->stream);
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int worst = STK_OK;
+  for (int i = 0; i < count; ++i) {
+    std::string e1;
+    const int rc = status[i] == cudaSuccess ? solve_finish(Ps[i], secs, infos ? &infos[i] : nullptr, e1)
+                                            : cuda_status(status[i], "solve", e1);
+    if (rc != STK_OK && (worst == STK_OK || rc != STK_ENOCONV)) {
+      worst = rc;
+      err = "problem " + std::to_string(i) + ": " + e1;
     }
+  }
   return worst;
 }
 
