@@ -88,6 +88,12 @@ typedef struct stk_options {
                             result up to rounding; on GB300 the default is faster for
                             every degree and precision (the patch kernel is bound by
                             shared-memory traffic, which the fused residual adds to). */
+  int direct_gemm;       /* FP32 smoothing with the Direct local solver, on levels with
+                            at least 512 interior patches per colour: 2 (default) the
+                            product P = M R of all interior patches of a colour is one
+                            GEMM on the tensor cores (cuBLAS, FP32 emulated by three
+                            BF16 terms); 1 the same GEMM in plain FP32 on the CUDA
+                            cores; 0 one product per patch inside the patch kernel. */
 } stk_options;
 
 typedef struct stk_problem stk_problem;

@@ -40,6 +40,7 @@ class Options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("use_graphs", ctypes.c_int),
         ("fused_smoother", ctypes.c_int),
+        ("direct_gemm", ctypes.c_int),
     ]
 
 
@@ -182,7 +183,7 @@ class StokesMG:
     def __init__(self, n: int, k: int, nu: float = 1.0, *, precision: int = PREC_FP64, gmres_restart: int = 20,
                  max_iter: int = 200, local_cg_mode: int = CG_FIXED, local_cg_iters: int = 15,
                  local_cg_tol: float = 1e-8, penalty_factor: float = 1.0, use_graphs: bool = True,
-                 fused_smoother: bool = False, dim: int = 3, stream=None):
+                 fused_smoother: bool = False, direct_gemm: int = 2, dim: int = 3, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -196,6 +197,7 @@ class StokesMG:
         opt.penalty_factor = penalty_factor
         opt.use_graphs = 1 if use_graphs else 0
         opt.fused_smoother = 1 if fused_smoother else 0
+        opt.direct_gemm = int(direct_gemm)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         opt.stream = ctypes.c_void_p(s.cuda_stream)

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <new>
 
+#include <cublas_v2.h>
+
 #include "internal.h"
 
 namespace {
@@ -59,6 +61,11 @@ void free_level(stk::Level& L) {
   if (L.flat32) cudaFree(L.flat32);
   L.flat64 = nullptr;
   L.flat32 = nullptr;
+  if (L.gemmR) cudaFree(L.gemmR);
+  if (L.gemmP) cudaFree(L.gemmP);
+  L.gemmR = nullptr;
+  L.gemmP = nullptr;
+  L.gemm_cap = 0;
 }
 
 void free_problem(stk_problem* P) {
@@ -75,6 +82,8 @@ void free_problem(stk_problem* P) {
   if (K.state_host) cudaFreeHost(K.state_host);
   for (cudaStream_t s : K.side)
     if (s) cudaStreamDestroy(s);
+  if (P->blas) cublasDestroy(static_cast<cublasHandle_t>(P->blas));
+  if (P->blas_ws) cudaFree(P->blas_ws);
   if (P->xfer64) cudaFree(P->xfer64);
   if (P->xfer32) cudaFree(P->xfer32);
   if (P->pmean_w) cudaFree(P->pmean_w);
@@ -144,6 +153,7 @@ int stk_default_options(stk_options* opt) {
   opt->stream = nullptr;
   opt->use_graphs = 1;
   opt->fused_smoother = 0;
+  opt->direct_gemm = 2;
   return STK_OK;
 }
 

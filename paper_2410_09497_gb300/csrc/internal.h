@@ -195,6 +195,12 @@ struct Level {
   float* dirM32 = nullptr;
   const double** dirtab64 = nullptr;
   const float** dirtab32 = nullptr;
+  const float* dir32_host[64] = {};  // the FP32 inverses' device addresses, per type, on the host
+  // FP32 Direct as one GEMM per colour: the interior patches' R and P
+  // (gemm_cap patches of (2k+2)^3 entries each)
+  float* gemmR = nullptr;
+  float* gemmP = nullptr;
+  int64_t gemm_cap = 0;
   // two dimensions: the 1D cell tables flattened with runtime sizes (the
   // order of stk_cell_tables), device copies in both precisions
   double* flat64 = nullptr;
@@ -260,6 +266,9 @@ struct stk_problem {
   double* coarse3[3] = {nullptr, nullptr, nullptr};  // FP64 b, x, r of a 3^3 coarse mesh
   std::shared_ptr<stk::Coarse3Factors> coarse3f;      // dense factors of the 3^3 coarse problem (shared)
   std::shared_ptr<stk::PlanarInverses> pinv2;         // 2D patch inverses (shared)
+  void* blas = nullptr;            // cuBLAS handle of the Direct solver's GEMM (created on first use)
+  void* blas_ws = nullptr;         // its workspace
+  size_t blas_ws_bytes = 0;
   stk::MgWork mg[2];               // [STK_F64], [STK_F32]
   stk::KrylovWork kry;
   std::string err;

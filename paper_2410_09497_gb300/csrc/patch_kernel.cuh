@@ -82,6 +82,13 @@ struct PatchArgs {
   int cg_iters;   // FIXED: exact count; TOL: limit
   int cg_tol_mode;
   T cg_tol;
+  // Direct local solver as one GEMM per colour (mode 0, interior launch):
+  // phase 1 writes each patch's mean-free Schur right-hand side R to
+  // rout[blk * NP ...] and stops; phase 2 reads the solution P = M R from
+  // pin[blk * NP ...] and finishes the patch (0: the product in the kernel)
+  int gemm_phase;
+  T* rout;
+  const T* pin;
 };
 
 // Per-problem fields of a multi-problem colour launch (passed by value).
@@ -809,34 +816,46 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   patch_pass<K, T, VEL_FWD, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
   patch_pass<K, T, VEL_FWD, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
   patch_pass<K, T, VEL_FWD, EPI_FT_AND_SCALE, EO_ALL>(Ba, Ft, 2, false, nullptr, Bb, tb, g);
-  // ---- R = sum_c (B_c S_c) Bb_c - G
-  patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 0, false, nullptr, nullptr, tb, g);
-  patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
-  patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
-  T s1 = T(0), s2 = T(0);
-  for (int q = tid; q < C::NP; q += C::NT) {
-    const int o = (q % NPD) + BX * (q / NPD);
-    const T r = (Ba[o] + Ba[BOX + o] + Ba[2 * BOX + o]) - Pp[o];
-    R[o] = r;
-    s1 += r;
+  // ---- R = sum_c (B_c S_c) Bb_c - G (not needed when P comes from the GEMM)
+  T s1 = T(0), s2 = T(0), mean = T(0), rr = T(0), rr0 = T(0);
+  if (A.gemm_phase != 2) {
+    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 0, false, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
+    for (int q = tid; q < C::NP; q += C::NT) {
+      const int o = (q % NPD) + BX * (q / NPD);
+      const T r = (Ba[o] + Ba[BOX + o] + Ba[2 * BOX + o]) - Pp[o];
+      R[o] = r;
+      s1 += r;
+    }
+    mean = block_sum<T, C::NW>(s1, red_a) / T(C::NP);
+    s2 = T(0);
+    for (int q = tid; q < C::NP; q += C::NT) {
+      const int o = (q % NPD) + BX * (q / NPD);
+      const T r = R[o] - mean;
+      R[o] = r;
+      Dd[o] = r;
+      Pp[o] = T(0);
+      s2 += r * r;
+    }
+    rr = block_sum<T, C::NW>(s2, red_b);
+    rr0 = rr;
   }
-  T mean = block_sum<T, C::NW>(s1, red_a) / T(C::NP);
-  s2 = T(0);
-  for (int q = tid; q < C::NP; q += C::NT) {
-    const int o = (q % NPD) + BX * (q / NPD);
-    const T r = R[o] - mean;
-    R[o] = r;
-    Dd[o] = r;
-    Pp[o] = T(0);
-    s2 += r * r;
+  if (A.gemm_phase == 1) {  // R leaves for the colour's GEMM
+    for (int q = tid; q < C::NP; q += C::NT) A.rout[(int64_t)blk * C::NP + q] = R[(q % NPD) + BX * (q / NPD)];
+    return;
   }
-  T rr = block_sum<T, C::NW>(s2, red_b);
-  const T rr0 = rr;
+  if (A.gemm_phase == 2) {  // P = M R from the colour's GEMM
+    for (int q = tid; q < C::NP; q += C::NT) Pp[(q % NPD) + BX * (q / NPD)] = A.pin[(int64_t)blk * C::NP + q];
+    __syncthreads();
+  }
 
   // ---- the local Schur system S P = R on mean-free pressures: Direct (a
   // precomputed (S + a 1 1^T)^{-1} of this patch type, which maps a mean-free
   // R to the mean-free solution) or conjugate gradients
-  const T* Mdir = ((A.mode == 0 || FUSED) && A.dir) ? A.dir[g.type[0] + 4 * g.type[1] + 16 * g.type[2]] : nullptr;
+  const T* Mdir = ((A.mode == 0 || FUSED) && A.dir && A.gemm_phase == 0)
+                      ? A.dir[g.type[0] + 4 * g.type[1] + 16 * g.type[2]]
+                      : nullptr;
   if (Mdir) {
     // 16-byte loads where the vectors of a column keep every thread busy
     // (19 % faster at k = 3 in FP32), else one output per load: thread t
@@ -871,7 +890,7 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
       }
     __syncthreads();
   }
-  for (int it = 0; !Mdir && it < A.cg_iters; ++it) {
+  for (int it = 0; !Mdir && A.gemm_phase == 0 && it < A.cg_iters; ++it) {
     if (A.cg_tol_mode && rr <= A.cg_tol * A.cg_tol * rr0) break;
     if (!(rr > T(0))) break;
     T* SDc = schur_apply();

@@ -16,6 +16,8 @@
 // columns and the 2^3 coarse solve.  The patch kernels (gather, Schur-CG
 // or Direct local solve by fast diagonalization, scatter) are in
 // patch_kernel.cuh.
+#include <cublas_v2.h>
+
 #include <algorithm>
 
 #include "patch_kernel.cuh"
@@ -76,7 +78,48 @@ static void fill_common(const stk_problem* P, const Level& L, PatchArgs<T>& a) {
   a.ctab = nullptr;
   a.part = 0;
   a.dir = nullptr;
+  a.gemm_phase = 0;
+  a.rout = nullptr;
+  a.pin = nullptr;
   for (int d = 0; d < 3; ++d) a.tlo[d] = a.cint[d] = a.btype[d] = 0;
+}
+
+constexpr int kGemmMinPatches = 512;  // interior patches per colour from which the Direct product is a GEMM
+
+// The cuBLAS handle and workspace of a problem (first call outside any
+// capture: the smoothing step that builds the Direct inverses makes it).
+static cudaError_t ensure_blas(stk_problem* P, size_t ws_bytes) {
+  if (!P->blas) {
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    P->blas = h;
+  }
+  if (P->blas_ws_bytes < ws_bytes) {
+    if (P->blas_ws) cudaFree(P->blas_ws);
+    P->blas_ws = nullptr;
+    P->blas_ws_bytes = 0;
+    cudaError_t e = dev_alloc(&P->blas_ws, ws_bytes);
+    if (e != cudaSuccess) return e;
+    P->blas_ws_bytes = ws_bytes;
+  }
+  cublasHandle_t h = static_cast<cublasHandle_t>(P->blas);
+  if (cublasSetWorkspace(h, P->blas_ws, P->blas_ws_bytes) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+  return cudaSuccess;
+}
+
+// P = M R for the `ni` interior patches of a colour: C (np x ni) = M (np x np)
+// R (np x ni), column-major; M symmetric, the type-0 inverse of the level
+static cudaError_t direct_gemm(const stk_problem* P, const Level& L, int ni) {
+  const int np = (2 * P->k + 2) * (2 * P->k + 2) * (2 * P->k + 2);
+  cublasHandle_t h = static_cast<cublasHandle_t>(P->blas);
+  if (cublasSetStream(h, P->stream) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+  const float one = 1.0f, zero = 0.0f;
+  const cublasComputeType_t ct =
+      P->opt.direct_gemm == 2 ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : CUBLAS_COMPUTE_32F_PEDANTIC;
+  const cublasStatus_t st = cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, np, ni, np, &one, L.dir32_host[0], CUDA_R_32F,
+                                         np, L.gemmR, CUDA_R_32F, np, &zero, L.gemmP, CUDA_R_32F, np, ct,
+                                         CUBLAS_GEMM_DEFAULT);
+  return st == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
 }
 
 constexpr int kSplitInterior = 8192;  // interior patches per colour from which they get their own launch
@@ -139,6 +182,28 @@ static cudaError_t patch_colour(const stk_problem* P, const Level& L, const Patc
   }
   interior_box(L.n, colour, cnt, a.tlo, a.cint);
   const int ni = a.cint[0] * a.cint[1] * a.cint[2];
+  // FP32 Direct: the interior patches' products as one GEMM (M read once per
+  // colour instead of once per patch), then the boundary patches as usual
+  if constexpr (sizeof(T) == 4) {
+    if (a.dir && !xin && P->opt.direct_gemm && L.eo_interior && ni >= kGemmMinPatches && L.gemm_cap >= ni &&
+        P->blas && L.dir32_host[0]) {
+      a.part = 1;
+      a.gemm_phase = 1;
+      a.rout = L.gemmR;
+      cudaError_t e = dispatch_patch<T>(P->k, a, ni, P->stream);
+      if (e == cudaSuccess) e = direct_gemm(P, L, ni);
+      if (e != cudaSuccess) return e;
+      a.gemm_phase = 2;
+      a.rout = nullptr;
+      a.pin = L.gemmP;
+      e = dispatch_patch<T>(P->k, a, ni, P->stream);
+      if (e != cudaSuccess || ni == nb) return e;
+      a.gemm_phase = 0;
+      a.pin = nullptr;
+      a.part = 2;
+      return dispatch_patch<T>(P->k, a, nb, P->stream);
+    }
+  }
   // Interior patches in their own launch (no dense transforms compiled in),
   // then the rest: 3-9 % faster per smoothing step at 64^3 (k = 2..4); at
   // 32^3 and below the second launch and its serialized tail cost as much.
@@ -321,16 +386,36 @@ cudaError_t ensure_direct(stk_problem* P, int level) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.dirtab64, t64.data(), sizeof(double*) * 64, cudaMemcpyHostToDevice, P->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.dirtab32, t32.data(), sizeof(float*) * 64, cudaMemcpyHostToDevice, P->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  // the GEMM form of the FP32 product: R and P of the most interior patches
+  // any colour has, and the cuBLAS handle (never during a capture: the first
+  // smoothing step of the level runs this)
+  int64_t ni_max = 0;
+  for (int colour = 0; colour < 8; ++colour) {
+    int cnt[3], tlo[3], cint[3];
+    colour_counts(L.n, colour, cnt);
+    interior_box(L.n, colour, cnt, tlo, cint);
+    ni_max = std::max<int64_t>(ni_max, (int64_t)cint[0] * cint[1] * cint[2]);
+  }
+  if (e == cudaSuccess && P->opt.direct_gemm && L.eo_interior && ni_max >= kGemmMinPatches && present[0]) {
+    e = dev_alloc(&L.gemmR, sizeof(float) * (size_t)(ni_max * np));
+    if (e == cudaSuccess) e = dev_alloc(&L.gemmP, sizeof(float) * (size_t)(ni_max * np));
+    if (e == cudaSuccess) e = ensure_blas(P, std::max<size_t>(size_t(64) << 20, sizeof(float) * 3 * (size_t)(ni_max * np)));
+    if (e == cudaSuccess) L.gemm_cap = ni_max;
+  }
   if (e != cudaSuccess) {
     cudaStreamSynchronize(P->stream);
-    for (void* p : {(void*)L.dirM64, (void*)L.dirM32, (void*)L.dirtab64, (void*)L.dirtab32})
+    for (void* p : {(void*)L.dirM64, (void*)L.dirM32, (void*)L.dirtab64, (void*)L.dirtab32, (void*)L.gemmR, (void*)L.gemmP})
       if (p) cudaFree(p);
     L.dirM64 = nullptr;
     L.dirM32 = nullptr;
     L.dirtab64 = nullptr;
     L.dirtab32 = nullptr;
+    L.gemmR = nullptr;
+    L.gemmP = nullptr;
+    L.gemm_cap = 0;
     return e;
   }
+  for (int c = 0; c < 64; ++c) L.dir32_host[c] = t32[c];
   L.dir_ready = true;
   return cudaSuccess;
 }
