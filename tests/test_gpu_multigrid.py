@@ -334,3 +334,27 @@ def test_autotuned_smoother_keeps_parity(stk):
     P.smooth(x, dev(b))
     check(relerr(x.cpu().numpy(), ref), 1e-12)
     P.close()
+
+
+@pytest.mark.parametrize("n,k", [(32, 2), (32, 3), (16, 4)])
+def test_direct_gemm_equals_per_patch_product(stk, n, k):
+    """The FP32 Direct smoother with the interior patches' products of a
+    colour as one GEMM (tensor cores with the FP32 emulation, or plain FP32)
+    equals the per-patch product in the patch kernel to FP32 rounding; FP64 is
+    unaffected (always the per-patch product)."""
+    import torch
+
+    x0 = None
+    out = {}
+    for mode in (0, 1, 2):
+        P = stk.StokesMG(n, k, local_cg_mode=stk.LOCAL_DIRECT, direct_gemm=mode)
+        N = P.layout()["n_total"]
+        if x0 is None:
+            x0 = random_vector(1800 + n + k, N)
+            b = random_vector(1900 + n + k, N)
+        x = dev(x0.astype(np.float32))
+        P.smooth(x, dev(b.astype(np.float32)))
+        out[mode] = x.cpu().numpy().astype(float)
+        P.close()
+    check(relerr(out[1], out[0]), 1e-5, "fp32 gemm")
+    check(relerr(out[2], out[0]), 1e-5, "bf16x9 gemm")
