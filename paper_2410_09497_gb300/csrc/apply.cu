@@ -222,9 +222,26 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
   T tcar = T(0), ucar = T(0), zcar = T(0);
   __syncthreads();
   const T sj = tab.S[bj], sl = tab.S[bl], ss = sj * sl;
-  // FP32: the 1D penalty rows of this thread's two discontinuous nodes live in
-  // registers for the whole march (FP64 reads them from shared memory).
+  // FP64: the 1D penalty rows with the mass of the other discontinuous
+  // direction folded in, so that t = M_d2 L_d1 u + M_d1 L_d2 u is one sum of
+  // products (two fewer FP64 operations per node), read from a shared table
+  // of every (boundary type, mass node, row) (registers are the FP64
+  // kernel's occupancy limit).  FP32 keeps this thread's two plain rows in
+  // registers for the whole march and scales the two sums (the FP32 kernel
+  // is latency-bound; the folded form cost it register spills).
   constexpr bool ROWREG = sizeof(T) == 4;
+  constexpr int RW = 3 * ND;  // one scaled row: LS, LLO, LHI
+  __shared__ T srow[ROWREG ? 1 : 3 * ND * ND * RW];
+  if constexpr (!ROWREG) {
+    for (int i = tid; i < 3 * ND * ND * RW; i += NT) {
+      const int qq = i % RW, b = (i / RW) % ND, sidx = (i / (RW * ND)) % ND, t = i / (RW * ND * ND);
+      const T v = qq < ND ? tab.LS[t][b * ND + qq] : (qq < 2 * ND ? tab.LLO[b * ND + qq - ND] : tab.LHI[b * ND + qq - 2 * ND]);
+      srow[i] = tab.S[sidx] * v;
+    }
+    __syncthreads();
+  }
+  const T* row1 = ROWREG ? nullptr : srow + ((typej * ND + bl) * ND + bj) * RW;
+  const T* row2 = ROWREG ? nullptr : srow + ((typel * ND + bj) * ND + bl) * RW;
   T r1s[ND], r1lo[ND], r1hi[ND], r2s[ND], r2lo[ND], r2hi[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) {
@@ -285,21 +302,38 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
         if (a < a0) continue;
         const T* row = &U[(a * J + tl + H) * J];
         const int bj0 = tj - bj + H;
-        T acc1 = T(0), acc2 = T(0);
-#pragma unroll
-        for (int q = 0; q < ND; ++q) {
-          acc1 += (ROWREG ? r1s[q] : tab.LS[typej][bj * ND + q]) * row[bj0 + q];
-          acc1 += (ROWREG ? r1lo[q] : tab.LLO[bj * ND + q]) * row[bj0 - ND + q];
-          acc1 += (ROWREG ? r1hi[q] : tab.LHI[bj * ND + q]) * row[bj0 + ND + q];
-        }
         const int bl0 = tl - bl + H;
+        if constexpr (ROWREG) {
+          T acc1 = T(0), acc2 = T(0);
 #pragma unroll
-        for (int q = 0; q < ND; ++q) {
-          acc2 += (ROWREG ? r2s[q] : tab.LS[typel][bl * ND + q]) * U[(a * J + bl0 + q) * J + tj + H];
-          acc2 += (ROWREG ? r2lo[q] : tab.LLO[bl * ND + q]) * U[(a * J + bl0 - ND + q) * J + tj + H];
-          acc2 += (ROWREG ? r2hi[q] : tab.LHI[bl * ND + q]) * U[(a * J + bl0 + ND + q) * J + tj + H];
+          for (int q = 0; q < ND; ++q) {
+            acc1 += r1s[q] * row[bj0 + q];
+            acc1 += r1lo[q] * row[bj0 - ND + q];
+            acc1 += r1hi[q] * row[bj0 + ND + q];
+          }
+#pragma unroll
+          for (int q = 0; q < ND; ++q) {
+            acc2 += r2s[q] * U[(a * J + bl0 + q) * J + tj + H];
+            acc2 += r2lo[q] * U[(a * J + bl0 - ND + q) * J + tj + H];
+            acc2 += r2hi[q] * U[(a * J + bl0 + ND + q) * J + tj + H];
+          }
+          tv[a] = sl * acc1 + sj * acc2;
+        } else {
+          T acc = T(0);
+#pragma unroll
+          for (int q = 0; q < ND; ++q) {
+            acc += row1[q] * row[bj0 + q];
+            acc += row1[ND + q] * row[bj0 - ND + q];
+            acc += row1[2 * ND + q] * row[bj0 + ND + q];
+          }
+#pragma unroll
+          for (int q = 0; q < ND; ++q) {
+            acc += row2[q] * U[(a * J + bl0 + q) * J + tj + H];
+            acc += row2[ND + q] * U[(a * J + bl0 - ND + q) * J + tj + H];
+            acc += row2[2 * ND + q] * U[(a * J + bl0 + ND + q) * J + tj + H];
+          }
+          tv[a] = acc;
         }
-        tv[a] = sl * acc1 + sj * acc2;
         uv[a] = ss * U[(a * J + tl + H) * J + tj + H];
       }
       // contraction along c, even-odd form (ContractTables)
