@@ -707,6 +707,9 @@ static cudaError_t issue_cycle_end(stk_problem* P, const double* b, double* x, c
   return cudaGetLastError();
 }
 
+// the step of the last solve launch that failed (for the error message)
+thread_local const char* g_solve_step = "";
+
 static cudaError_t read_state(stk_problem* P, size_t bytes) {
   cudaError_t e = cudaMemcpyAsync(P->kry.state_host, P->kry.state, bytes, cudaMemcpyDeviceToHost, P->stream);
   return e == cudaSuccess ? cudaStreamSynchronize(P->stream) : e;
@@ -782,6 +785,7 @@ static cudaError_t build_solve_graph(stk_problem* P, const double* b, double* x,
   }
   if (e1 == cudaSuccess) e1 = issue_start(P, b, x, rtol, hout, 1);
   if (e1 == cudaSuccess) e1 = add_while(main, &hout, &outer, false);
+  if (e1 != cudaSuccess) g_solve_step = "graph build: start and outer loop";
   if (e1 == cudaSuccess) {
     // outer body on side stream 0
     e1 = cudaStreamBeginCaptureToGraph(K.side[0], outer, nullptr, nullptr, 0, mode);
@@ -802,6 +806,7 @@ static cudaError_t build_solve_graph(stk_problem* P, const double* b, double* x,
           cudaGraph_t got = nullptr;
           eb = cudaStreamEndCapture(K.side[1], &got);
           if (ei != cudaSuccess) eb = ei;
+          if (eb != cudaSuccess) g_solve_step = "graph build: Arnoldi step body";
           P->stream = K.side[0];
         }
       }
@@ -823,7 +828,10 @@ static cudaError_t build_solve_graph(stk_problem* P, const double* b, double* x,
     if (K.solve_graph) cudaGraphExecDestroy(K.solve_graph);
     K.solve_graph = nullptr;
     e = cudaGraphInstantiate(&K.solve_graph, graph, 0);
-    if (e != cudaSuccess) K.solve_graph = nullptr;
+    if (e != cudaSuccess) {
+      K.solve_graph = nullptr;
+      g_solve_step = "graph instantiate";
+    }
   }
   if (graph) cudaGraphDestroy(graph);
   if (e == cudaSuccess) {
@@ -840,14 +848,20 @@ static bool use_solve_graph(const stk_problem* P) { return P->opt.use_graphs && 
 // without graphs the host drives the same launches, reading the state's flags
 // after each step.  Returns after the GPU work is enqueued (graph) or done.
 static cudaError_t solve_launch(stk_problem* P, const double* b, double* x, double rtol) {
+  g_solve_step = "setup";
   cudaError_t e = prepare_solve(P);
   if (e != cudaSuccess) return e;
   KrylovWork& K = P->kry;
   if (use_solve_graph(P)) {
+    g_solve_step = "graph build";
     if (!K.solve_graph || K.key_b != b || K.key_x != x || K.key_rtol != rtol) e = build_solve_graph(P, b, x, rtol);
-    if (e == cudaSuccess) e = cudaGraphLaunch(K.solve_graph, P->stream);
+    if (e == cudaSuccess) {
+      g_solve_step = "graph launch";
+      e = cudaGraphLaunch(K.solve_graph, P->stream);
+    }
     return e;
   }
+  g_solve_step = "host-driven steps";
   GmresState* st = static_cast<GmresState*>(K.state);
   const GmresState* sh = static_cast<const GmresState*>(K.state_host);
   e = issue_start(P, b, x, rtol, 0, 0);
@@ -889,7 +903,7 @@ static int solve_finish(stk_problem* P, double t0_seconds, stk_solve_info* info,
 }
 
 static int cuda_status(cudaError_t e, const char* what, std::string& err) {
-  err = std::string(what) + ": " + cudaGetErrorString(e);
+  err = std::string(what) + " (" + g_solve_step + "): " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA;
 }
 
