@@ -831,6 +831,7 @@ static cudaError_t build_solve_graph(stk_problem* P, const double* b, double* x,
     if (e != cudaSuccess) {
       K.solve_graph = nullptr;
       g_solve_step = "graph instantiate";
+      cudaGetLastError();  // a refused instantiation is not a sticky error: do not leave it for later calls
     }
   }
   if (graph) cudaGraphDestroy(graph);
@@ -842,7 +843,18 @@ static cudaError_t build_solve_graph(stk_problem* P, const double* b, double* x,
   return e;
 }
 
-static bool use_solve_graph(const stk_problem* P) { return P->opt.use_graphs && P->stream != nullptr; }
+// The whole solve is one graph when the problem has a stream and graphs are
+// on, except when its FP32 Direct smoother runs the interior patches'
+// products as cuBLAS GEMMs: the library's kernels cannot sit in a
+// conditional node's body (instantiation is refused), so those solves are
+// driven by the host, with the V-cycle replayed as its own graph.
+static bool use_solve_graph(const stk_problem* P) {
+  if (!P->opt.use_graphs || P->stream == nullptr) return false;
+  if (P->opt.precision == STK_PREC_MIXED && P->opt.local_cg_mode == STK_LOCAL_DIRECT && P->opt.direct_gemm)
+    for (const Level& L : P->levels)
+      if (L.gemm_cap > 0) return false;
+  return true;
+}
 
 // Start a solve: the graph is (re)built for new b, x or rtol and launched;
 // without graphs the host drives the same launches, reading the state's flags

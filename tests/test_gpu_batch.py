@@ -188,3 +188,30 @@ def test_fused_smoother_equals_split_smoother(stk, n, k):
             check(float((ya - yb).abs().max() / yb.abs().max()), bar, f"colour 5 mode={mode} {dt}")
         fused.close()
         split.close()
+
+
+@pytest.mark.parametrize("n,k,mode,prec", [(24, 3, "direct", "mixed"), (12, 2, "direct", "fp64"), (16, 2, "cg", "mixed")])
+def test_stream_solves_direct_and_cg(stk, n, k, mode, prec):
+    """Solves on a stream of their own (the whole solve as one graph, or, for
+    the FP32 Direct smoother with its cuBLAS GEMM, host-driven with the
+    V-cycle graph) converge, and equal the solve with graphs off bitwise."""
+    import torch
+
+    from seeded_inputs import manufactured_coefficients
+
+    local = stk.LOCAL_DIRECT if mode == "direct" else stk.CG_FIXED
+    precision = stk.PREC_MIXED if prec == "mixed" else stk.PREC_FP64
+    out = []
+    for graphs in (True, False):
+        s = torch.cuda.Stream()
+        P = stk.StokesMG(n, k, 1.0, precision=precision, stream=s, local_cg_mode=local, use_graphs=graphs)
+        b = torch.empty(P.layout()["n_total"], dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(s):
+            P.rhs(manufactured_coefficients(950), b)
+        x = torch.zeros_like(b)
+        for _ in range(2):  # the second solve replays what the first built
+            info = P.solve(b, x, rtol=1e-8)
+        assert info["converged"] and info["relres"] <= 1e-8
+        out.append(x.cpu().numpy())
+        P.close()
+    assert np.array_equal(out[0], out[1])
