@@ -50,7 +50,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # cells (x larger than L2), scaled to the benchmarked mesh by its velocity
 # DoFs.  Valid only for the kernel version it was taken on; other keys report
 # null.
-DRAM_TRAFFIC = {(3, 64, "f64"): 1247200000}
+DRAM_TRAFFIC = {}
 
 
 def velocity_flops_per_dof(k: int) -> float:
