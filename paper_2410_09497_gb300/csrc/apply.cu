@@ -242,6 +242,33 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
   }
   const T* row1 = ROWREG ? nullptr : srow + ((typej * ND + bl) * ND + bj) * RW;
   const T* row2 = ROWREG ? nullptr : srow + ((typel * ND + bj) * ND + bl) * RW;
+  // FP64: the blocks of the contraction that act on u and p (EK, OK, ED, OD)
+  // with this thread's cross-section mass S[bj] S[bl] folded in, one table
+  // per (bj, bl), so that neither u nor p is scaled per node
+  constexpr int CP = NC / 2, CQ = ND / 2;
+  constexpr int CNE = CP + (NC % 2), CQE = CQ + (ND % 2);
+  constexpr int SCW = CNE * CNE + CP * CP + CNE * CQ + CP * CQE;  // one (bj, bl) table
+  __shared__ T sct[ROWREG ? 1 : ND * ND * SCW];
+  if constexpr (!ROWREG) {
+    for (int i = tid; i < ND * ND * SCW; i += NT) {
+      const int w = i % SCW, sb = i / SCW, b1 = sb / ND, b2 = sb % ND;
+      T v;
+      if (w < CNE * CNE)
+        v = A.ce.EK[(w / CNE) * kMaxC + w % CNE];
+      else if (w < CNE * CNE + CP * CP)
+        v = A.ce.OK[((w - CNE * CNE) / CP) * kMaxC + (w - CNE * CNE) % CP];
+      else if (w < CNE * CNE + CP * CP + CNE * CQ) {
+        const int o = w - CNE * CNE - CP * CP;
+        v = CQ > 0 ? A.ce.ED[(o / (CQ > 0 ? CQ : 1)) * kMaxD + o % (CQ > 0 ? CQ : 1)] : T(0);
+      } else {
+        const int o = w - CNE * CNE - CP * CP - CNE * CQ;
+        v = A.ce.OD[(o / CQE) * kMaxD + o % CQE];
+      }
+      sct[i] = tab.S[b1] * tab.S[b2] * v;
+    }
+    __syncthreads();
+  }
+  const T* ctab = ROWREG ? nullptr : sct + (bj * ND + bl) * SCW;
   T r1s[ND], r1lo[ND], r1hi[ND], r2s[ND], r2lo[ND], r2hi[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) {
@@ -279,7 +306,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
     T pv[ND], bv[ND];
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
-      pv[q] = ss * pv_next[q];
+      pv[q] = ROWREG ? ss * pv_next[q] : pv_next[q];
       bv[q] = b_next[q];
     }
     const bool has_next = cc + 1 < cc1;
@@ -334,7 +361,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
           }
           tv[a] = acc;
         }
-        uv[a] = ss * U[(a * J + tl + H) * J + tj + H];
+        uv[a] = ROWREG ? ss * U[(a * J + tl + H) * J + tj + H] : U[(a * J + tl + H) * J + tj + H];
       }
       // contraction along c, even-odd form (ContractTables)
       constexpr int P = NC / 2, Q = ND / 2;
@@ -362,14 +389,18 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
       for (int i = 0; i < NE; ++i) {
         T ze = T(0), zo = T(0);
 #pragma unroll
-        for (int a = 0; a < NE; ++a) ze += A.ce.EK[i * kMaxC + a] * ue[a] + A.ce.EM[i * kMaxC + a] * te[a];
+        for (int a = 0; a < NE; ++a)
+          ze += (ROWREG ? A.ce.EK[i * kMaxC + a] : ctab[i * NE + a]) * ue[a] + A.ce.EM[i * kMaxC + a] * te[a];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) ze += A.ce.ED[i * kMaxD + q] * po[q];
+        for (int q = 0; q < Q; ++q)
+          ze += (ROWREG ? A.ce.ED[i * kMaxD + q] : ctab[NE * NE + P * P + i * Q + q]) * po[q];
         if (i < P) {
 #pragma unroll
-          for (int a = 0; a < P; ++a) zo += A.ce.OK[i * kMaxC + a] * uo[a] + A.ce.OM[i * kMaxC + a] * to[a];
+          for (int a = 0; a < P; ++a)
+            zo += (ROWREG ? A.ce.OK[i * kMaxC + a] : ctab[NE * NE + i * P + a]) * uo[a] + A.ce.OM[i * kMaxC + a] * to[a];
 #pragma unroll
-          for (int q = 0; q < QE; ++q) zo += A.ce.OD[i * kMaxD + q] * pe[q];
+          for (int q = 0; q < QE; ++q)
+            zo += (ROWREG ? A.ce.OD[i * kMaxD + q] : ctab[NE * NE + P * P + NE * Q + i * QE + q]) * pe[q];
           z[i] = ze + zo;
           z[NC - 1 - i] = ze - zo;
         } else {
