@@ -338,8 +338,9 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
                     stk_solve_info* infos);
 
 /* Autotuner (no counterpart in the paper): for every level, time the operator
- * apply in `dtype` with each candidate march length of its velocity kernel
- * (cells per CTA: n, n/2, ..., 2) on the problem's stream and keep the
+ * apply in `dtype` with each candidate run length of its velocity kernel's
+ * persistent march (cells per run along the continuous direction: n, then
+ * halving down to 2) on the problem's stream and keep the
  * fastest, then, on every level that is smoothed, one smoothing step in each
  * form (fused_smoother 0 and 1, with the problem's local solver) and keep
  * the faster; every later apply, residual, smoothing step and solve of that
@@ -354,9 +355,18 @@ int stk_autotune(stk_problem* P, int dtype);
  * in the paper. */
 int stk_tuned_smoother(const stk_problem* P, int level, int dtype, int* fused);
 
-/* The march length chosen by stk_autotune for a level and dtype (0 = not
- * tuned: the built-in choice is used); no counterpart in the paper. */
-int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_cta);
+/* The run length chosen by stk_autotune (or set by stk_set_tuning) for a
+ * level and dtype (0 = not tuned: the built-in choice is used, whole columns
+ * in FP64, about 8 CTAs per SM in FP32); no counterpart in the paper. */
+int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_run);
+
+/* Set the run length of the apply's persistent march for a level and dtype
+ * (cells per run along the continuous direction; 0 restores the built-in
+ * choice; values above n act as n); for reusing a tuning found earlier.
+ * Drops the problem's captured graphs of that dtype (synchronises its
+ * stream).  STK_EINVAL for a bad level, dtype or a negative value; 2D
+ * problems have no such tuning (STK_EINVAL).  No counterpart in the paper. */
+int stk_set_tuning(stk_problem* P, int level, int dtype, int cells_per_run);
 
 /* b = right-hand side of a manufactured problem on the finest level
  * (Sec. 3.3): velocity rows (f, phi_i) with f = -nu Laplace(u) + grad p and

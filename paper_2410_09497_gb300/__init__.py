@@ -96,6 +96,7 @@ def load_library():
         "stk_smooth_colour": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
         "stk_autotune": (ctypes.c_int, [P, ctypes.c_int]),
         "stk_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "stk_set_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "stk_tuned_smoother": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_smooth_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P)]),
@@ -314,9 +315,9 @@ class StokesMG:
         return x
 
     def autotune(self, dtype: int = F32, with_smoother: bool = False):
-        """Time the apply's march length per level (and the smoother's form on the
-        smoothed levels) for dtype and keep the fastest; returns {level: cells_per_cta}
-        or, with with_smoother, {level: (cells_per_cta, fused)}."""
+        """Time the apply's march run length per level (and the smoother's form on
+        the smoothed levels) for dtype and keep the fastest; returns
+        {level: cells_per_run} or, with with_smoother, {level: (cells_per_run, fused)}."""
         self._check(self.lib.stk_autotune(self.h, int(dtype)))
         out = {}
         for level in range(self.num_levels):
@@ -325,6 +326,10 @@ class StokesMG:
             self._check(self.lib.stk_tuned_smoother(self.h, level, int(dtype), ctypes.byref(f)))
             out[level] = (v.value, f.value) if with_smoother else v.value
         return out
+
+    def set_tuning(self, level: int, dtype: int, cells_per_run: int):
+        """Set the apply's march run length of a level and dtype (0: built-in choice)."""
+        self._check(self.lib.stk_set_tuning(self.h, self._lvl(level), int(dtype), int(cells_per_run)))
 
     def coarse_solve(self, b, x):
         """x = A_0^+ b on level 0."""

@@ -562,6 +562,18 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
   return STK_OK;
 }
 
+// A V-cycle graph captured before a change of tuning replays the old launch
+// shapes: drop it so that the next solve captures the new ones.
+static void drop_graphs(stk_problem* P, int dtype) {
+  stk::MgWork& W = P->mg[dtype];
+  cudaStreamSynchronize(P->stream);
+  if (W.graph) cudaGraphExecDestroy(W.graph);
+  W.graph = nullptr;
+  W.vcycle_runs = 0;
+  if (P->kry.solve_graph) cudaGraphExecDestroy(P->kry.solve_graph);  // holds the V-cycle's launches too
+  P->kry.solve_graph = nullptr;
+}
+
 int stk_autotune(stk_problem* P, int dtype) {
   if (!P) return STK_EINVAL;
   int rc = check_3d(P, "autotune");
@@ -580,8 +592,9 @@ int stk_autotune(stk_problem* P, int dtype) {
     if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, L.ntotal * es, P->stream);
     float best = 1e30f;
     int best_chunk = 0;
-    // candidate march lengths: the whole column down to 2 cells per CTA
-    for (int chunk = L.n; e == cudaSuccess && chunk >= 2; chunk /= 2) {
+    // candidate run lengths of the persistent march: n, then halving to 2
+    for (int chunk = L.n;; chunk = (chunk + 1) / 2) {
+      if (e != cudaSuccess) break;
       L.apply_chunk[dtype] = chunk;
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = stk::launch_apply(P, (int)l, dtype, x, nullptr, y, 1.0);
       if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
@@ -594,6 +607,7 @@ int stk_autotune(stk_problem* P, int dtype) {
         best = ms;
         best_chunk = chunk;
       }
+      if (chunk <= 2) break;
     }
     L.apply_chunk[dtype] = best_chunk;
     // the smoother's form on the levels that are smoothed (all but the
@@ -617,15 +631,7 @@ int stk_autotune(stk_problem* P, int dtype) {
     if (x) cudaFree(x);
     if (y) cudaFree(y);
   }
-  // a V-cycle graph captured before tuning replays the old launch shapes:
-  // drop it so that the next solve captures the tuned ones
-  stk::MgWork& W = P->mg[dtype];
-  cudaStreamSynchronize(P->stream);
-  if (W.graph) cudaGraphExecDestroy(W.graph);
-  W.graph = nullptr;
-  W.vcycle_runs = 0;
-  if (P->kry.solve_graph) cudaGraphExecDestroy(P->kry.solve_graph);  // holds the V-cycle's launches too
-  P->kry.solve_graph = nullptr;
+  drop_graphs(P, dtype);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return status_of(P, e, "autotune");
@@ -638,10 +644,21 @@ int stk_tuned_smoother(const stk_problem* P, int level, int dtype, int* fused) {
   return STK_OK;
 }
 
-int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_cta) {
-  if (!P || !cells_per_cta || level < 0 || level >= (int)P->levels.size() || (dtype != STK_F64 && dtype != STK_F32))
+int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_run) {
+  if (!P || !cells_per_run || level < 0 || level >= (int)P->levels.size() || (dtype != STK_F64 && dtype != STK_F32))
     return STK_EINVAL;
-  *cells_per_cta = P->levels[level].apply_chunk[dtype];
+  *cells_per_run = P->levels[level].apply_chunk[dtype];
+  return STK_OK;
+}
+
+int stk_set_tuning(stk_problem* P, int level, int dtype, int cells_per_run) {
+  if (!P) return STK_EINVAL;
+  int rc = check_3d(P, "set_tuning");
+  if (rc) return rc;
+  if (level < 0 || level >= (int)P->levels.size() || (dtype != STK_F64 && dtype != STK_F32) || cells_per_run < 0)
+    return fail(P, STK_EINVAL, "set_tuning: level, dtype or cells per run out of range");
+  P->levels[level].apply_chunk[dtype] = cells_per_run;
+  drop_graphs(P, dtype);
   return STK_OK;
 }
 

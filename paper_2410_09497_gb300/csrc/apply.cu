@@ -11,8 +11,10 @@
 // plus eq. `weak_form` integrated exactly: face terms of eq. `bilinear` only
 // see tangential components, whose jumps live in the discontinuous directions.
 //
-// Velocity kernel: one CTA owns a tile of (d1, d2) node lines and marches
-// along the continuous direction c through a chunk of cells.  Per cell it
+// Velocity kernel: a CTA works on a tile of (d1, d2) node lines and marches
+// along the continuous direction c through a run of cells (a persistent CTA
+// takes an equal share of all columns' cells, possibly several runs).  Per
+// cell it
 // stages the k+1 new node layers of u_c (plus one cell of halo in d1 and d2)
 // in shared memory, forms t = M_d2 L_d1 u + M_d1 L_d2 u per node, and then
 // contracts along c in registers with the cell matrices KC, MC and D^T, in
@@ -20,7 +22,7 @@
 // reflection of the cell, so the contraction works on sums and differences of
 // mirrored nodes with half the products (ContractTables).  The
 // contribution of a cell to its upper shared node is carried to the next step,
-// so no face or node is computed twice inside a chunk; a chunk re-does only
+// so no face or node is computed twice inside a run; a run re-does only
 // the cell below it.  Pressure kernel: one thread per pressure node.
 #include <algorithm>
 
@@ -37,7 +39,8 @@ struct ApplyArgs {
   CellTables<T> tv;      // by value: constant-bank operands for compile-time indices
   ContractTables<T> ce;  // even-odd contraction along c, by value
   int n, m;
-  int chunk, nchunks, ntile;
+  int ntile;
+  int chunk;  // cells per run of the persistent march along c
 };
 
 template <int K>
@@ -169,27 +172,36 @@ __device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, cons
     if (pl.sidx[i] >= 0) U[pl.sidx[i]] = regs[i];
 }
 
-// Resident CTAs per SM: 2 for k <= 4, 3 for the 2-cell tiles of k = 5.  One
-// CTA per SM (the register count the compiler picks unbounded) left the FP64
-// pipe half idle at k = 4 and 5; the register cap costs a few spills there and
-// measured 1.2-1.3x faster at 64^3.
+// Whether the velocity kernel marches persistently (FP64 up to k = 4; the
+// k = 5 kernel spills and measured 2 % slower that way) or one run per CTA.
+template <int K, typename T>
+__host__ __device__ constexpr bool velocity_persistent() {
+  return sizeof(T) == 8 && K <= 4;
+}
+
+// One run of the velocity march: cells cc0 .. cc1-1 of column col
+// (component c = col / tiles, tile col % tiles), after a carry-only step for
+// the cell below cc0 when cc0 > 0.  U is the staging buffer, srow / sct the
+// FP64 row and contraction tables.
 template <int K, typename T, bool RES>
-__global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_velocity_kernel(ApplyArgs<T> A) {
+__device__ __forceinline__ void march_run(const ApplyArgs<T>& A, const CellTables<T>& tab, T* __restrict__ U,
+                                          const T* __restrict__ srow, const T* __restrict__ sct, int col, int cc0,
+                                          int cc1) {
   using Cfg = ApplyCfg<K>;
   constexpr int ND = Cfg::ND, NC = Cfg::NC, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
-  __shared__ CellTables<T> tab;
-  extern __shared__ __align__(16) unsigned char apply_smem[];
-  T* U = reinterpret_cast<T*>(apply_smem);  // [NC][J][J] staged layers, jj fastest
-
-  const int c = blockIdx.y;
-  const int d1 = (c == 0) ? 1 : 0;
-  const int d2 = (c == 2) ? 1 : 2;
-  int bid = blockIdx.x;
-  const int chunk = bid % A.nchunks;
-  bid /= A.nchunks;
-  const int j0 = (bid % A.ntile) * TJ, l0 = (bid / A.ntile) * TJ;
+  constexpr bool ROWREG = sizeof(T) == 4;
+  constexpr int RW = 3 * ND;
+  constexpr int CP = NC / 2, CQ = ND / 2;
+  constexpr int CNE = CP + (NC % 2), CQE = CQ + (ND % 2);
+  constexpr int SCW = CNE * CNE + CP * CP + CNE * CQ + CP * CQE;
   const int tid = threadIdx.x, tj = tid % TJ, tl = tid / TJ;
   const int m = A.m, n = A.n;
+  const int tiles = A.ntile * A.ntile;
+
+  const int c = col / tiles, tile = col - c * tiles;
+  const int d1 = (c == 0) ? 1 : 0;
+  const int d2 = (c == 2) ? 1 : 2;
+  const int j0 = (tile % A.ntile) * TJ, l0 = (tile / A.ntile) * TJ;
   const int jn = j0 + tj, ln = l0 + tl;
   const bool active = (jn < m) && (ln < m);
 
@@ -208,66 +220,16 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
   T* yc = A.y + c * nvel;
   const T* bc = RES ? A.b + c * nvel : nullptr;
 
-  for (int i = tid; i < (int)(sizeof(CellTables<T>) / sizeof(T)); i += NT)
-    reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(&A.tv)[i];
-
   const int cj = jn / ND, bj = jn - cj * ND, cl = ln / ND, bl = ln - cl * ND;
   const int typej = (cj == 0) ? 1 : ((cj == n - 1) ? 2 : 0);
   const int typel = (cl == 0) ? 1 : ((cl == n - 1) ? 2 : 0);
   const int64_t line_off = (int64_t)jn * s1 + (int64_t)ln * s2;
   const int64_t pline_off = (int64_t)jn * ps1 + (int64_t)ln * ps2;
 
-  const int cc0 = chunk * A.chunk;
-  const int cc1 = min(n, cc0 + A.chunk);
   T tcar = T(0), ucar = T(0), zcar = T(0);
-  __syncthreads();
   const T sj = tab.S[bj], sl = tab.S[bl], ss = sj * sl;
-  // FP64: the 1D penalty rows with the mass of the other discontinuous
-  // direction folded in, so that t = M_d2 L_d1 u + M_d1 L_d2 u is one sum of
-  // products (two fewer FP64 operations per node), read from a shared table
-  // of every (boundary type, mass node, row) (registers are the FP64
-  // kernel's occupancy limit).  FP32 keeps this thread's two plain rows in
-  // registers for the whole march and scales the two sums (the FP32 kernel
-  // is latency-bound; the folded form cost it register spills).
-  constexpr bool ROWREG = sizeof(T) == 4;
-  constexpr int RW = 3 * ND;  // one scaled row: LS, LLO, LHI
-  __shared__ T srow[ROWREG ? 1 : 3 * ND * ND * RW];
-  if constexpr (!ROWREG) {
-    for (int i = tid; i < 3 * ND * ND * RW; i += NT) {
-      const int qq = i % RW, b = (i / RW) % ND, sidx = (i / (RW * ND)) % ND, t = i / (RW * ND * ND);
-      const T v = qq < ND ? tab.LS[t][b * ND + qq] : (qq < 2 * ND ? tab.LLO[b * ND + qq - ND] : tab.LHI[b * ND + qq - 2 * ND]);
-      srow[i] = tab.S[sidx] * v;
-    }
-    __syncthreads();
-  }
   const T* row1 = ROWREG ? nullptr : srow + ((typej * ND + bl) * ND + bj) * RW;
   const T* row2 = ROWREG ? nullptr : srow + ((typel * ND + bj) * ND + bl) * RW;
-  // FP64: the blocks of the contraction that act on u and p (EK, OK, ED, OD)
-  // with this thread's cross-section mass S[bj] S[bl] folded in, one table
-  // per (bj, bl), so that neither u nor p is scaled per node
-  constexpr int CP = NC / 2, CQ = ND / 2;
-  constexpr int CNE = CP + (NC % 2), CQE = CQ + (ND % 2);
-  constexpr int SCW = CNE * CNE + CP * CP + CNE * CQ + CP * CQE;  // one (bj, bl) table
-  __shared__ T sct[ROWREG ? 1 : ND * ND * SCW];
-  if constexpr (!ROWREG) {
-    for (int i = tid; i < ND * ND * SCW; i += NT) {
-      const int w = i % SCW, sb = i / SCW, b1 = sb / ND, b2 = sb % ND;
-      T v;
-      if (w < CNE * CNE)
-        v = A.ce.EK[(w / CNE) * kMaxC + w % CNE];
-      else if (w < CNE * CNE + CP * CP)
-        v = A.ce.OK[((w - CNE * CNE) / CP) * kMaxC + (w - CNE * CNE) % CP];
-      else if (w < CNE * CNE + CP * CP + CNE * CQ) {
-        const int o = w - CNE * CNE - CP * CP;
-        v = CQ > 0 ? A.ce.ED[(o / (CQ > 0 ? CQ : 1)) * kMaxD + o % (CQ > 0 ? CQ : 1)] : T(0);
-      } else {
-        const int o = w - CNE * CNE - CP * CP - CNE * CQ;
-        v = A.ce.OD[(o / CQE) * kMaxD + o % CQE];
-      }
-      sct[i] = tab.S[b1] * tab.S[b2] * v;
-    }
-    __syncthreads();
-  }
   const T* ctab = ROWREG ? nullptr : sct + (bj * ND + bl) * SCW;
   T r1s[ND], r1lo[ND], r1hi[ND], r2s[ND], r2lo[ND], r2hi[ND];
 #pragma unroll
@@ -290,7 +252,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
   if constexpr (PIPE) stage_plan<K, NREG>(plan, c, j0, l0, m, s1, s2, sc);
   T pv_next[ND], b_next[ND];
   const int cstart = (cc0 > 0 ? cc0 - 1 : 0);
-  // the first step of a CTA computes its bottom node; later steps carry it
+  // the first step of a run computes its bottom node; later steps carry it
   stage_layers<K, T, NC>(U, u, 0, c, cstart, j0, l0, m, sc, s1, s2);
   if (active) {
 #pragma unroll
@@ -301,7 +263,7 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
   }
   __syncthreads();
   for (int cc = cstart; cc < cc1; ++cc) {
-    const bool warm = cc < cc0;  // carry-only step for the cell below the chunk
+    const bool warm = cc < cc0;  // carry-only step for the cell below the run
     const int a0 = (cc == cstart) ? 0 : 1;
     T pv[ND], bv[ND];
 #pragma unroll
@@ -433,6 +395,114 @@ __global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_veloc
   }
 }
 
+// Resident CTAs per SM: 2 for k <= 4, 3 for the 2-cell tiles of k = 5.  One
+// CTA per SM (the register count the compiler picks unbounded) left the FP64
+// pipe half idle at k = 4 and 5; the register cap costs a few spills there and
+// measured 1.2-1.3x faster at 64^3.
+template <int K, typename T, bool RES>
+__global__ void __launch_bounds__(ApplyCfg<K>::NT, (K <= 4 ? 2 : 3)) apply_velocity_kernel(ApplyArgs<T> A) {
+  using Cfg = ApplyCfg<K>;
+  constexpr int ND = Cfg::ND, NC = Cfg::NC, NT = Cfg::NT;
+  __shared__ CellTables<T> tab;
+  extern __shared__ __align__(16) unsigned char apply_smem[];
+  T* U = reinterpret_cast<T*>(apply_smem);  // [NC][J][J] staged layers, jj fastest
+
+  const int tid = threadIdx.x;
+  const int n = A.n;
+  for (int i = tid; i < (int)(sizeof(CellTables<T>) / sizeof(T)); i += NT)
+    reinterpret_cast<T*>(&tab)[i] = reinterpret_cast<const T*>(&A.tv)[i];
+  __syncthreads();
+  // FP64: the 1D penalty rows with the mass of the other discontinuous
+  // direction folded in, so that t = M_d2 L_d1 u + M_d1 L_d2 u is one sum of
+  // products (two fewer FP64 operations per node), read from a shared table
+  // of every (boundary type, mass node, row) (registers are the FP64
+  // kernel's occupancy limit).  FP32 keeps this thread's two plain rows in
+  // registers for the whole march and scales the two sums (the FP32 kernel
+  // is latency-bound; the folded form cost it register spills).
+  constexpr bool ROWREG = sizeof(T) == 4;
+  constexpr int RW = 3 * ND;  // one scaled row: LS, LLO, LHI
+  __shared__ T srow[ROWREG ? 1 : 3 * ND * ND * RW];
+  if constexpr (!ROWREG) {
+    for (int i = tid; i < 3 * ND * ND * RW; i += NT) {
+      const int qq = i % RW, b = (i / RW) % ND, sidx = (i / (RW * ND)) % ND, t = i / (RW * ND * ND);
+      const T v = qq < ND ? tab.LS[t][b * ND + qq] : (qq < 2 * ND ? tab.LLO[b * ND + qq - ND] : tab.LHI[b * ND + qq - 2 * ND]);
+      srow[i] = tab.S[sidx] * v;
+    }
+    __syncthreads();
+  }
+  // FP64: the blocks of the contraction that act on u and p (EK, OK, ED, OD)
+  // with this thread's cross-section mass S[bj] S[bl] folded in, one table
+  // per (bj, bl), so that neither u nor p is scaled per node
+  constexpr int CP = NC / 2, CQ = ND / 2;
+  constexpr int CNE = CP + (NC % 2), CQE = CQ + (ND % 2);
+  constexpr int SCW = CNE * CNE + CP * CP + CNE * CQ + CP * CQE;  // one (bj, bl) table
+  __shared__ T sct[ROWREG ? 1 : ND * ND * SCW];
+  if constexpr (!ROWREG) {
+    for (int i = tid; i < ND * ND * SCW; i += NT) {
+      const int w = i % SCW, sb = i / SCW, b1 = sb / ND, b2 = sb % ND;
+      T v;
+      if (w < CNE * CNE)
+        v = A.ce.EK[(w / CNE) * kMaxC + w % CNE];
+      else if (w < CNE * CNE + CP * CP)
+        v = A.ce.OK[((w - CNE * CNE) / CP) * kMaxC + (w - CNE * CNE) % CP];
+      else if (w < CNE * CNE + CP * CP + CNE * CQ) {
+        const int o = w - CNE * CNE - CP * CP;
+        v = CQ > 0 ? A.ce.ED[(o / (CQ > 0 ? CQ : 1)) * kMaxD + o % (CQ > 0 ? CQ : 1)] : T(0);
+      } else {
+        const int o = w - CNE * CNE - CP * CP - CNE * CQ;
+        v = A.ce.OD[(o / CQE) * kMaxD + o % CQE];
+      }
+      sct[i] = tab.S[b1] * tab.S[b2] * v;
+    }
+    __syncthreads();
+  }
+
+  // Every column (component c, tile of (d1, d2) lines, n cells along c) is
+  // cut into runs of `chunk` cells (the last one shorter), numbered column by
+  // column.  FP32 (latency-bound, register-capped) and the spilling FP64
+  // kernel of k = 5: one run per CTA, the grid covers every run.  FP64 up to
+  // k = 4 (bound by the FP64 pipe): a balanced persistent march over one wave
+  // of resident CTAs.  Round r of G = gridDim.x CTAs:
+  // CTA g marches run g + r G, as long as a whole round remains, so the CTAs
+  // of a round work on neighbouring tiles at the same heights and find the
+  // halos they stage in L2.  The cells of the remaining runs (fewer than G)
+  // are then split evenly: each CTA takes an equal contiguous range of them
+  // in column order, which may start or end inside a run and span several,
+  // so that all CTAs finish together and no partial last wave idles the SMs.
+  constexpr bool PERSIST = velocity_persistent<K, T>();
+  const int tiles = A.ntile * A.ntile, ncol = 3 * tiles, chunk = A.chunk;
+  const int nch = (n + chunk - 1) / chunk;  // runs per column
+  int rounds = 1, f = 0, fend = 0, r = 0;
+  if constexpr (PERSIST) {
+    const int G = gridDim.x;
+    rounds = (ncol * nch) / G;
+    const int u_rest = rounds * G;  // first run of the split remainder
+    const int64_t f_rest = (int64_t)(u_rest / nch) * n + (int64_t)(u_rest % nch) * chunk;
+    const int64_t rest = (int64_t)ncol * n - f_rest;
+    f = (int)(f_rest + rest * blockIdx.x / G);
+    fend = (int)(f_rest + rest * (blockIdx.x + 1) / G);
+  }
+  for (;;) {
+    int col, cc0, cc1;
+    if (r < rounds) {
+      const int u = blockIdx.x + r * gridDim.x;
+      ++r;
+      col = u / nch;
+      cc0 = (u - col * nch) * chunk;
+      cc1 = min(n, cc0 + chunk);
+    } else if (PERSIST && f < fend) {
+      col = f / n;
+      cc0 = f - col * n;
+      cc1 = min(n, cc0 + (fend - f));
+      f += cc1 - cc0;
+    } else {
+      break;
+    }
+    march_run<K, T, RES>(A, tab, U, srow, sct, col, cc0, cc1);
+    if constexpr (!PERSIST) break;
+  }
+}
+
 template <int K, typename T>
 __global__ void __launch_bounds__(256) apply_pressure_kernel(ApplyArgs<T> A) {
   constexpr int ND = K + 1, NC = K + 2;
@@ -469,6 +539,39 @@ __global__ void __launch_bounds__(256) apply_pressure_kernel(ApplyArgs<T> A) {
   }
 }
 
+// Resident CTAs of the velocity kernel on the whole GPU (one wave) and the SM count.
+template <int K, typename T>
+static cudaError_t velocity_wave(bool res, int* wave, int* nsm) {
+  using Cfg = ApplyCfg<K>;
+  const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
+  static std::atomic<unsigned long long> smem_set{0}, smem_set_res{0};
+  static std::atomic<int> occ_plain{0}, occ_res{0};
+  auto* kern = res ? apply_velocity_kernel<K, T, true> : apply_velocity_kernel<K, T, false>;
+  cudaError_t e = allow_dynamic_smem(kern, smem, res ? smem_set_res : smem_set);
+  if (e != cudaSuccess) return e;
+  std::atomic<int>& occ = res ? occ_res : occ_plain;
+  int per_sm = occ.load();
+  if (per_sm == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+    occ.store(per_sm);
+  }
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *nsm = std::max(sms, 1);
+  *wave = per_sm * *nsm;
+  return e;
+}
+
+// cells of all (component, tile) columns of a level
+template <int K>
+static int64_t velocity_cells(const Level& L) {
+  const int ntile = (L.m + ApplyCfg<K>::TJ - 1) / ApplyCfg<K>::TJ;
+  return 3LL * ntile * ntile * L.n;
+}
+
 template <int K, typename T>
 static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, const ContractTables<T>& ce, const T* x,
                                   const T* b, T* y, T alpha, int stages, cudaStream_t s) {
@@ -485,27 +588,30 @@ static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, cons
   a.n = L.n;
   a.m = L.m;
   a.ntile = (L.m + Cfg::TJ - 1) / Cfg::TJ;
-  const int tiles = a.ntile * a.ntile;
-  // cells marched per CTA: tuned value if stk_autotune chose one, else enough
-  // CTAs for ~8 per SM with marches of at least 4 cells
-  const int tuned = L.apply_chunk[sizeof(T) == 8 ? STK_F64 : STK_F32];
-  int nch = (1216 + 3 * tiles - 1) / (3 * tiles);
-  nch = std::max(1, std::min(nch, L.n / 4 > 0 ? L.n / 4 : 1));
-  a.chunk = tuned > 0 ? std::min(tuned, L.n) : (L.n + nch - 1) / nch;
-  a.nchunks = (L.n + a.chunk - 1) / a.chunk;
-  dim3 grid(tiles * a.nchunks, 3);
-  const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
-  static std::atomic<unsigned long long> smem_set{0}, smem_set_res{0};
+  a.chunk = L.n;
   if (stages & 1) {
-    if (b) {
-      const cudaError_t e = allow_dynamic_smem(apply_velocity_kernel<K, T, true>, smem, smem_set_res);
-      if (e != cudaSuccess) return e;
-      apply_velocity_kernel<K, T, true><<<grid, Cfg::NT, smem, s>>>(a);
-    } else {
-      const cudaError_t e = allow_dynamic_smem(apply_velocity_kernel<K, T, false>, smem, smem_set);
-      if (e != cudaSuccess) return e;
-      apply_velocity_kernel<K, T, false><<<grid, Cfg::NT, smem, s>>>(a);
-    }
+    int wave = 0, nsm = 1;
+    const cudaError_t e = velocity_wave<K, T>(b != nullptr, &wave, &nsm);
+    if (e != cudaSuccess) return e;
+    // cells per run: the tuned value if set; else the persistent march takes
+    // whole columns on one wave of resident CTAs (at least 4 cells each), and
+    // one run per CTA cuts the columns so that there are about 8 CTAs per SM
+    // with runs of at least 4 cells
+    const int64_t total = velocity_cells<K>(L);
+    const int tiles = a.ntile * a.ntile;
+    const int tuned = L.apply_chunk[sizeof(T) == 8 ? STK_F64 : STK_F32];
+    int nch = (8 * nsm + 3 * tiles - 1) / (3 * tiles);
+    nch = std::max(1, std::min(nch, L.n / 4 > 0 ? L.n / 4 : 1));
+    constexpr bool persist = velocity_persistent<K, T>();
+    a.chunk = tuned > 0 ? std::min(tuned, L.n) : (persist ? L.n : (L.n + nch - 1) / nch);
+    const int64_t runs = 3LL * tiles * ((L.n + a.chunk - 1) / a.chunk);
+    const int64_t grid =
+        persist ? std::max<int64_t>(1, std::min<int64_t>(wave, total / 4)) : runs;
+    const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
+    if (b)
+      apply_velocity_kernel<K, T, true><<<(unsigned)grid, Cfg::NT, smem, s>>>(a);
+    else
+      apply_velocity_kernel<K, T, false><<<(unsigned)grid, Cfg::NT, smem, s>>>(a);
   }
   if (stages & 2) {
     const int64_t np = (int64_t)L.m * L.m * L.m;

@@ -182,7 +182,7 @@ struct Level {
   CellTables<float> htab32{};
   ContractTables<double> hce64{};       // even-odd contraction tables, by value
   ContractTables<float> hce32{};
-  int apply_chunk[2] = {0, 0};          // cells per CTA march of the apply ([dtype]); 0 = default
+  int apply_chunk[2] = {0, 0};          // cells per run of the apply's velocity march ([dtype]); 0 = default
   int fused_pick[2] = {-1, -1};         // smoother form chosen by stk_autotune ([dtype]); -1 = the option's
   PatchTables<double>* ptab64 = nullptr;  // device
   PatchTables<float>* ptab32 = nullptr;   // device

@@ -14,7 +14,8 @@ from _parity import check
 
 pytestmark = pytest.mark.gpu
 
-# (n, k): several tiles, ragged tails, chunked marches and every degree
+# (n, k): several tiles, ragged tails, runs that start inside a column or span
+# several (the default grid gives CTAs ~4 cells each on small meshes) and every degree
 CASES = [(2, 1), (6, 1), (12, 1), (3, 2), (8, 2), (4, 3), (6, 3), (3, 4), (6, 4), (2, 5), (4, 5)]
 
 
@@ -116,6 +117,7 @@ def test_autotuned_apply_keeps_parity(stk, dtype_name):
     P = stk.StokesMG(n, k, 1.0)
     dt = stk.F64 if dtype_name == "f64" else stk.F32
     tuned = P.autotune(dt)
+    # run length of the persistent velocity march: n, halved down to 2
     assert all(2 <= v <= P.layout(level)["n"] for level, v in tuned.items())
     x = random_vector(4242, d.N)
     tdt = torch.float64 if dtype_name == "f64" else torch.float32
@@ -124,4 +126,29 @@ def test_autotuned_apply_keeps_parity(stk, dtype_name):
     P.apply(xd, yd)
     ref = A @ (xd.cpu().double().numpy() * d.free_mask())
     assert _relerr(yd.cpu().double().numpy(), ref) <= (1e-12 if dtype_name == "f64" else 1e-5)
+    P.close()
+
+
+@pytest.mark.parametrize("n,k,blk", [(12, 2, 5), (12, 3, 1), (6, 4, 4), (16, 1, 3), (4, 5, 3)])
+def test_set_tuning_run_lengths_keep_parity(stk, n, k, blk):
+    """Every run length of the persistent march (ragged last runs, runs of one
+    cell, remainders split across CTAs) gives the assembled operator's
+    product; 0 restores the built-in choice."""
+    import torch
+
+    d = Discretization(n, k)
+    A = d.assemble()
+    P = stk.StokesMG(n, k, 1.0)
+    x = random_vector(4343 + n + k, d.N)
+    ref = A @ (x * d.free_mask())
+    for dt, tdt, bar in ((stk.F64, torch.float64, 1e-12), (stk.F32, torch.float32, 1e-5)):
+        P.set_tuning(-1, dt, blk)
+        xd = torch.from_numpy(x).to(tdt).cuda()
+        yd = torch.full_like(xd, float("nan"))
+        P.apply(xd, yd)
+        r = A @ (xd.cpu().double().numpy() * d.free_mask())
+        check(_relerr(yd.cpu().double().numpy(), r), bar, f"blk={blk} {tdt}")
+        P.set_tuning(-1, dt, 0)
+    with pytest.raises(stk.StokesError):
+        P.set_tuning(0, stk.F64, -1)
     P.close()

@@ -10,7 +10,8 @@ addresses and against the oracle's own numbering:
   oracle's patch DoF set R_j in the same order, stay inside the vector, touch
   no constrained boundary-normal DoF, and give disjoint sets to the patches of
   one colour (the scatter x += R_j^T (U, P) has no atomics).
-* operator apply: the (tile, chunk) decomposition of the pencil march writes
+* operator apply: the persistent CTAs' equal shares of all columns' cells,
+  numbered block row by block row and marched as runs inside blocks, write
   every velocity entry exactly once, and the 32-bit per-CTA staging offsets
   fit for every mesh the library accepts.
 * level transfers: the prolongation's plain += reaches every free fine node
@@ -122,50 +123,115 @@ def test_patch_index_map_equals_the_oracle_patch_sets(n, k):
 
 
 # ---------------------------------------------------------------- apply kernel
-# Restated from launch_apply_k (apply.cu): BJ cells per tile side, the march
-# length per CTA and the chunks of the continuous direction.
+# Restated from launch_apply_k and apply_velocity_kernel (apply.cu): BJ cells
+# per tile side; every column cut into runs of `chunk` cells, numbered column
+# by column.  FP32 and FP64 at k = 5: one run per CTA (chunk from ~8 CTAs
+# per SM, runs of at least 4 cells).  FP64 up to k = 4: one wave of G CTAs
+# (at least 4 cells each) marching
+# whole columns; whole rounds of G runs go round-robin (CTA g takes run
+# g + r G), and the cells of the remaining runs are split evenly into
+# contiguous ranges in column order.
 
 BJ = {1: 8, 2: 5, 3: 4, 4: 3, 5: 2}
 
 
-def apply_grid(n, k, tuned=0):
+def apply_grid(n, k, tuned, wave, f64, nsm=152):
+    f64 = f64 and k <= 4  # the persistent march
     nd = k + 1
     m = n * nd
     tj = BJ[k] * nd
     ntile = (m + tj - 1) // tj
     tiles = ntile * ntile
-    nch = (1216 + 3 * tiles - 1) // (3 * tiles)
+    total = 3 * tiles * n
+    nch = (8 * nsm + 3 * tiles - 1) // (3 * tiles)
     nch = max(1, min(nch, n // 4 if n // 4 > 0 else 1))
-    chunk = min(tuned, n) if tuned > 0 else (n + nch - 1) // nch
-    nchunks = (n + chunk - 1) // chunk
-    return m, tj, ntile, chunk, nchunks
+    chunk = min(tuned, n) if tuned > 0 else (n if f64 else (n + nch - 1) // nch)
+    runs = 3 * tiles * ((n + chunk - 1) // chunk)
+    grid = max(1, min(wave, total // 4)) if f64 else runs
+    return m, tj, ntile, total, grid, chunk
+
+
+def apply_runs(n, k, tuned, wave, f64):
+    """(CTA, component, tile, cc0, cc1) of every run, as the kernel walks them."""
+    m, tj, ntile, total, grid, chunk = apply_grid(n, k, tuned, wave, f64)
+    f64 = f64 and k <= 4
+    tiles = ntile * ntile
+    ncol = 3 * tiles
+    nch = (n + chunk - 1) // chunk
+    rounds, f_rest = 1, ncol * n
+    if f64:
+        rounds = ncol * nch // grid
+        u_rest = rounds * grid
+        f_rest = (u_rest // nch) * n + (u_rest % nch) * chunk
+    rest = ncol * n - f_rest
+    runs = []
+    for g in range(grid):
+        for r in range(rounds):
+            u = g + r * grid
+            col, ch = divmod(u, nch)
+            cc0 = ch * chunk
+            runs.append((g, col // tiles, col % tiles, cc0, min(n, cc0 + chunk)))
+        if not f64:
+            continue
+        f, fend = f_rest + rest * g // grid, f_rest + rest * (g + 1) // grid
+        while f < fend:
+            col, cc0 = divmod(f, n)
+            cc1 = min(n, cc0 + (fend - f))
+            f += cc1 - cc0
+            runs.append((g, col // tiles, col % tiles, cc0, cc1))
+    return runs
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
-@pytest.mark.parametrize("n", [2, 3, 4, 6, 8, 12, 16, 24, 32])
-@pytest.mark.parametrize("tuned", [0, 1, 3, 7])
-def test_apply_march_writes_every_velocity_entry_once(n, k, tuned):
+@pytest.mark.parametrize("n", [2, 3, 4, 6, 8, 12, 16, 24])
+@pytest.mark.parametrize("tuned,wave,f64", [(0, 304, True), (0, 7, True), (0, 100000, True), (1, 304, True),
+                                            (3, 304, True), (5, 7, True), (1000, 304, True), (0, 304, False),
+                                            (1, 304, False), (3, 304, False), (1000, 304, False)])
+def test_apply_march_writes_every_velocity_entry_once(n, k, tuned, wave, f64):
     nd = k + 1
-    m, tj, ntile, chunk, nchunks = apply_grid(n, k, tuned)
+    m, tj, ntile, total, grid, chunk = apply_grid(n, k, tuned, wave, f64)
+    assert total < 2 ** 31 and grid < 2 ** 31
     # lines: the tiles cover [0, m)^2 with inactive threads past m
     lines = np.zeros((m, m), dtype=np.int32)
     for t in range(ntile * ntile):
         j0, l0 = (t % ntile) * tj, (t // ntile) * tj
         lines[j0:min(m, j0 + tj), l0:min(m, l0 + tj)] += 1
     assert (lines == 1).all()
-    # along the continuous direction: the chunks' written nodes plus the top node
-    written = np.zeros(m + 1, dtype=np.int32)
-    for ch in range(nchunks):
-        cc0, cc1 = ch * chunk, min(n, ch * chunk + chunk)
+    # along the continuous direction, per (component, tile) column: the runs'
+    # written nodes plus the top node
+    written = np.zeros((3, ntile * ntile, m + 1), dtype=np.int32)
+    cells = 0
+    for g, c, tile, cc0, cc1 in apply_runs(n, k, tuned, wave, f64):
+        assert 0 <= g < grid and 0 <= c < 3 and 0 <= tile < ntile * ntile and 0 <= cc0 < cc1 <= n
+        cells += cc1 - cc0
         cstart = cc0 - 1 if cc0 > 0 else 0
-        assert 0 <= cstart <= cc0 < cc1 <= n
         for cc in range(cstart, cc1):
             if cc < cc0:
-                continue  # carry-only step for the cell below the chunk
-            written[cc * nd: cc * nd + nd] += 1
+                continue  # carry-only step for the cell below the run
+            written[c, tile, cc * nd: cc * nd + nd] += 1
             if cc == n - 1:
-                written[m] += 1
+                written[c, tile, m] += 1
+    assert cells == total
     assert (written == 1).all()
+
+
+def test_apply_shares_are_balanced():
+    # FP64, one wave of 304 resident CTAs on a 64^3, k = 3 level (768 columns
+    # of 64 cells): two rounds of whole columns, then 160 columns split
+    # evenly: every CTA marches 161 or 162 cells
+    per, first = {}, {}
+    for g, c, tile, cc0, cc1 in apply_runs(64, 3, 0, 304, True):
+        per.setdefault(g, []).append((cc0, cc1))
+        first.setdefault(g, []).append(c * 256 + tile)
+    assert len(per) == 304
+    assert {sum(b - a for a, b in v) for v in per.values()} <= {161, 162}
+    assert all(v[0] == (0, 64) and v[1] == (0, 64) for v in per.values())
+    # round r: CTA g marches column g + 304 r, so the CTAs of a round work on
+    # neighbouring tiles
+    assert all(v[:2] == [g, g + 304] for g, v in first.items())
+    # FP32: 1536 CTAs of one 32-cell run each
+    m, tj, ntile, total, grid, chunk = apply_grid(64, 3, 0, 304, False)
+    assert (grid, chunk) == (1536, 32)
 
 
 def test_apply_staging_offsets_fit_in_32_bits():
