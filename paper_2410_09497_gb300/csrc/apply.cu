@@ -53,6 +53,22 @@ struct ApplyCfg {
   static constexpr int NT = TJ * TJ;                                          // threads per CTA
 };
 
+// Whether the velocity kernel marches persistently (FP64 up to k = 4; the
+// k = 5 kernel spills and measured 2 % slower that way) or one run per CTA.
+template <int K, typename T>
+__host__ __device__ constexpr bool velocity_persistent() {
+  return sizeof(T) == 8 && K <= 4;
+}
+
+// Row pitch of the staged layers: odd for the persistent FP64 kernels, so
+// that the two node rows a warp reads along d1 fall in different banks
+// (measured 4 % faster at k = 3, where the staged extent is 24; the FP32
+// kernel measured 3 % slower with the odd pitch).
+template <int K, typename T>
+struct StagePitch {
+  static constexpr int value = velocity_persistent<K, T>() ? (ApplyCfg<K>::J | 1) : ApplyCfg<K>::J;
+};
+
 // Stage NA node layers a0 .. a0+NA-1 of cell cc along c into U[a][ll][jj],
 // one cell of halo in d1 and d2 (corners skipped: never read).  Global memory
 // is walked in its own order (x fastest) so that loads coalesce.
@@ -86,7 +102,7 @@ __device__ __forceinline__ void stage_layers(T* __restrict__ U, const T* __restr
     const int gj = j0 - H + jj, gl = l0 - H + ll, ic = cc * ND + a;
     T v = T(0);
     if (gj >= 0 && gj < m && gl >= 0 && gl < m && ic > 0 && ic < m) v = u[ic * sc + gj * s1 + gl * s2];
-    U[(a * J + ll) * J + jj] = v;
+    U[(a * J + ll) * StagePitch<K, T>::value + jj] = v;
   }
 }
 
@@ -126,7 +142,7 @@ struct StagePlan {
   unsigned top;
 };
 
-template <int K, int NREG>
+template <int K, typename T, int NREG>
 __device__ __forceinline__ void stage_plan(StagePlan<NREG>& pl, int c, int j0, int l0, int m, int64_t s1,
                                            int64_t s2, int64_t sc) {
   using Cfg = ApplyCfg<K>;
@@ -143,7 +159,7 @@ __device__ __forceinline__ void stage_plan(StagePlan<NREG>& pl, int c, int j0, i
       stage_decode<K>(e, c, a, jj, ll);
       const bool hj = (jj < H) || (jj >= H + TJ), hl = (ll < H) || (ll >= H + TJ);
       if (!(hj && hl)) {
-        pl.sidx[i] = (a * J + ll) * J + jj;
+        pl.sidx[i] = (a * J + ll) * StagePitch<K, T>::value + jj;
         const int gj = j0 - H + jj, gl = l0 - H + ll;
         if (gj >= 0 && gj < m && gl >= 0 && gl < m) pl.goff[i] = (int)(a * sc + gj * s1 + gl * s2);
         if (a == ND) pl.top |= 1u << i;
@@ -172,13 +188,6 @@ __device__ __forceinline__ void stage_put(T* __restrict__ U, const T* regs, cons
     if (pl.sidx[i] >= 0) U[pl.sidx[i]] = regs[i];
 }
 
-// Whether the velocity kernel marches persistently (FP64 up to k = 4; the
-// k = 5 kernel spills and measured 2 % slower that way) or one run per CTA.
-template <int K, typename T>
-__host__ __device__ constexpr bool velocity_persistent() {
-  return sizeof(T) == 8 && K <= 4;
-}
-
 // One run of the velocity march: cells cc0 .. cc1-1 of column col
 // (component c = col / tiles, tile col % tiles), after a carry-only step for
 // the cell below cc0 when cc0 > 0.  U is the staging buffer, srow / sct the
@@ -189,6 +198,7 @@ __device__ __forceinline__ void march_run(const ApplyArgs<T>& A, const CellTable
                                           int cc1) {
   using Cfg = ApplyCfg<K>;
   constexpr int ND = Cfg::ND, NC = Cfg::NC, TJ = Cfg::TJ, H = Cfg::H, J = Cfg::J, NT = Cfg::NT;
+  constexpr int JP = StagePitch<K, T>::value;
   constexpr bool ROWREG = sizeof(T) == 4;
   constexpr int RW = 3 * ND;
   constexpr int CP = NC / 2, CQ = ND / 2;
@@ -249,7 +259,7 @@ __device__ __forceinline__ void march_run(const ApplyArgs<T>& A, const CellTable
   constexpr int NREG = PIPE ? (ND * J * J + NT - 1) / NT : 1;
   T nxt[NREG];
   StagePlan<NREG> plan;
-  if constexpr (PIPE) stage_plan<K, NREG>(plan, c, j0, l0, m, s1, s2, sc);
+  if constexpr (PIPE) stage_plan<K, T, NREG>(plan, c, j0, l0, m, s1, s2, sc);
   T pv_next[ND], b_next[ND];
   const int cstart = (cc0 > 0 ? cc0 - 1 : 0);
   // the first step of a run computes its bottom node; later steps carry it
@@ -289,7 +299,7 @@ __device__ __forceinline__ void march_run(const ApplyArgs<T>& A, const CellTable
 #pragma unroll
       for (int a = 0; a < NC; ++a) {
         if (a < a0) continue;
-        const T* row = &U[(a * J + tl + H) * J];
+        const T* row = &U[(a * J + tl + H) * JP];
         const int bj0 = tj - bj + H;
         const int bl0 = tl - bl + H;
         if constexpr (ROWREG) {
@@ -302,9 +312,9 @@ __device__ __forceinline__ void march_run(const ApplyArgs<T>& A, const CellTable
           }
 #pragma unroll
           for (int q = 0; q < ND; ++q) {
-            acc2 += r2s[q] * U[(a * J + bl0 + q) * J + tj + H];
-            acc2 += r2lo[q] * U[(a * J + bl0 - ND + q) * J + tj + H];
-            acc2 += r2hi[q] * U[(a * J + bl0 + ND + q) * J + tj + H];
+            acc2 += r2s[q] * U[(a * J + bl0 + q) * JP + tj + H];
+            acc2 += r2lo[q] * U[(a * J + bl0 - ND + q) * JP + tj + H];
+            acc2 += r2hi[q] * U[(a * J + bl0 + ND + q) * JP + tj + H];
           }
           tv[a] = sl * acc1 + sj * acc2;
         } else {
@@ -317,13 +327,13 @@ __device__ __forceinline__ void march_run(const ApplyArgs<T>& A, const CellTable
           }
 #pragma unroll
           for (int q = 0; q < ND; ++q) {
-            acc += row2[q] * U[(a * J + bl0 + q) * J + tj + H];
-            acc += row2[ND + q] * U[(a * J + bl0 - ND + q) * J + tj + H];
-            acc += row2[2 * ND + q] * U[(a * J + bl0 + ND + q) * J + tj + H];
+            acc += row2[q] * U[(a * J + bl0 + q) * JP + tj + H];
+            acc += row2[ND + q] * U[(a * J + bl0 - ND + q) * JP + tj + H];
+            acc += row2[2 * ND + q] * U[(a * J + bl0 + ND + q) * JP + tj + H];
           }
           tv[a] = acc;
         }
-        uv[a] = ROWREG ? ss * U[(a * J + tl + H) * J + tj + H] : U[(a * J + tl + H) * J + tj + H];
+        uv[a] = ROWREG ? ss * U[(a * J + tl + H) * JP + tj + H] : U[(a * J + tl + H) * JP + tj + H];
       }
       // contraction along c, even-odd form (ContractTables)
       constexpr int P = NC / 2, Q = ND / 2;
@@ -543,7 +553,7 @@ __global__ void __launch_bounds__(256) apply_pressure_kernel(ApplyArgs<T> A) {
 template <int K, typename T>
 static cudaError_t velocity_wave(bool res, int* wave, int* nsm) {
   using Cfg = ApplyCfg<K>;
-  const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
+  const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * StagePitch<K, T>::value;
   static std::atomic<unsigned long long> smem_set{0}, smem_set_res{0};
   static std::atomic<int> occ_plain{0}, occ_res{0};
   auto* kern = res ? apply_velocity_kernel<K, T, true> : apply_velocity_kernel<K, T, false>;
@@ -607,7 +617,7 @@ static cudaError_t launch_apply_k(const Level& L, const CellTables<T>& tab, cons
     const int64_t runs = 3LL * tiles * ((L.n + a.chunk - 1) / a.chunk);
     const int64_t grid =
         persist ? std::max<int64_t>(1, std::min<int64_t>(wave, total / 4)) : runs;
-    const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * Cfg::J;
+    const size_t smem = sizeof(T) * Cfg::NC * Cfg::J * StagePitch<K, T>::value;
     if (b)
       apply_velocity_kernel<K, T, true><<<(unsigned)grid, Cfg::NT, smem, s>>>(a);
     else
