@@ -365,7 +365,7 @@ int stk_tuning(const stk_problem* P, int level, int dtype, int* cells_per_run);
  * choice; values above n act as n); for reusing a tuning found earlier.
  * Drops the problem's captured graphs of that dtype (synchronises its
  * stream).  STK_EINVAL for a bad level, dtype or a negative value; 2D
- * problems have no such tuning (STK_EINVAL).  No counterpart in the paper. */
+ * problems have no such tuning (STK_EINVAL); no counterpart in the paper. */
 int stk_set_tuning(stk_problem* P, int level, int dtype, int cells_per_run);
 
 /* b = right-hand side of a manufactured problem on the finest level
