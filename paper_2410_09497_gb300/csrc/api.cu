@@ -268,6 +268,8 @@ int stk_setup(int n, int k, double nu, const stk_options* opt, stk_problem** out
     stk::PatchTables<float> p32;
     stk::fill_patch_tables(pt, &p64);
     stk::fill_patch_tables(pt, &p32);
+    L.hptab64 = p64;
+    L.hptab32 = p32;
     cudaError_t e = stk::dev_alloc(&L.tab64, sizeof(h64));
     if (e == cudaSuccess) e = stk::dev_alloc(&L.tab32, sizeof(h32));
     if (e == cudaSuccess) e = stk::dev_alloc(&L.ptab64, sizeof(p64));

@@ -186,6 +186,8 @@ struct Level {
   int fused_pick[2] = {-1, -1};         // smoother form chosen by stk_autotune ([dtype]); -1 = the option's
   PatchTables<double>* ptab64 = nullptr;  // device
   PatchTables<float>* ptab32 = nullptr;   // device
+  PatchTables<double> hptab64;            // host copies (the interior kernel's matrices go by value)
+  PatchTables<float> hptab32;
   bool eo_interior = false;  // continuous and interior 1D eigenbases both in even-odd order
   // Direct local solver (built on first use): (S + a 1 1^T)^{-1} of every patch
   // type of the level, column-major (2k+2)^3 squared, FP64 and FP32 copies, and

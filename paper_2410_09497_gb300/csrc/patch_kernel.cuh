@@ -40,24 +40,44 @@ struct PatchCfg {
   static constexpr int NP = NPD * NPD * NPD;
   static constexpr int BX = NPD + 1;           // padded x extent of every patch tensor
   static constexpr int BOX = BX * NPD * NPD;   // one padded tensor
-  // A pass transforms LPC lines of each component.  W warps serve one
-  // component (warp-uniform component: no divergence) and each thread
-  // transforms R lines with every matrix entry it loads: the broadcast loads
-  // of the transform matrices are what the shared-memory pipe spends most of
-  // its wavefronts on.
-  static constexpr int LPC = NPD * NPD;
-  static constexpr int W = (K <= 3) ? 1 : (K == 4 ? 2 : 3);
+  static constexpr int LPC = NPD * NPD;       // lines of one component along a direction
+};
+
+// Threads of a patch CTA.  A pass transforms LPC lines of each component.  W
+// warps serve one component (warp-uniform component: no divergence) and each
+// thread transforms R lines with every matrix entry it loads: the broadcast
+// loads of the transform matrices are what the shared-memory pipe spends most
+// of its wavefronts on.  FP32 at k = 3: two warps per component (one line per
+// thread, twice the warps per SM to hide the latency of the passes) measured
+// 5 % faster per smoothing step than one; FP64 at k = 3 measured 5 % slower
+// that way (register spills at 3 CTAs per SM).
+template <int K, typename T>
+struct PatchThreads {
+  static constexpr int W = sizeof(T) == 4 ? ((K <= 2) ? 1 : (K <= 4 ? 2 : 3)) : ((K <= 3) ? 1 : (K == 4 ? 2 : 3));
   static constexpr int TPC = 32 * W;
-  static constexpr int R = (LPC + TPC - 1) / TPC;
+  static constexpr int R = (PatchCfg<K>::LPC + TPC - 1) / TPC;
   static constexpr int NT = 3 * TPC;
   static constexpr int NW = NT / 32;
 };
 
+// The four transform matrices of an interior patch (every 1D basis of type
+// 0: SC, SD[0], EC, FM[0]), passed to the interior-patch kernel by value.
+// Their warp-uniform reads at compile-time offsets come from the constant
+// bank as FMA operands instead of shared-memory broadcasts, which the
+// shared-memory pipe (the interior kernel's bound) no longer has to serve.
+template <int K, typename T>
+struct InteriorMats {
+  static constexpr int NPD = 2 * K + 2;
+  T SC[NPD * kRowStride], SD[NPD * kRowStride], EC[NPD * kRowStride], FM[NPD * kRowStride];
+};
+
 // Resident CTAs per SM the register budget must allow: as many as the shared
-// memory of one patch (13 padded tensors + tables) permits.
+// memory of one patch (13 padded tensors + tables) permits, except FP32 at
+// k = 3, where 5 CTAs of 6 warps (68 registers a thread) measured 3 % faster
+// than the 6 shared memory allows (56 registers, with spills).
 template <int K, typename T>
 struct PatchOcc {
-  static constexpr int value = sizeof(T) == 4 ? ((K == 1) ? 12 : (K == 2) ? 8 : (K == 3) ? 6 : (K == 4) ? 3 : 2)
+  static constexpr int value = sizeof(T) == 4 ? ((K == 1) ? 12 : (K == 2) ? 8 : (K == 3) ? 5 : (K == 4) ? 3 : 2)
                                               : ((K == 1) ? 8 : (K == 2) ? 4 : (K == 3) ? 3 : 1);
 };
 
@@ -70,6 +90,7 @@ struct PatchArgs {
   const CellTables<T>* ctab;  // mode 3: the level's 1D cell matrices
   double* cols;   // mode 1: column-major output, N_p x N_p
   const PatchTables<T>* tab;
+  const PatchTables<T>* htab;  // host copy of *tab: the launcher passes the interior matrices from it
   int n, m;
   int colour;
   int cnt[3];     // patches of the colour per direction
@@ -170,6 +191,22 @@ __device__ __forceinline__ void vec_fma(double* r, const double2& w, double s) {
 __device__ __forceinline__ float vget(const float4& w, int e) { return e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w; }
 __device__ __forceinline__ double vget(const double2& w, int e) { return e == 0 ? w.x : w.y; }
 
+// VW consecutive entries of a transform matrix row, from M + off: one 16-byte
+// shared-memory load, or (SCAL) VW scalar reads, which the compiler takes
+// straight from the constant bank as FMA operands when M is a kernel
+// parameter and off is known at compile time.
+template <bool SCAL, typename T>
+__device__ __forceinline__ typename Vec16<T>::type mat_vec(const T* __restrict__ M, int off) {
+  if constexpr (SCAL) {
+    if constexpr (sizeof(T) == 4)
+      return make_float4(M[off], M[off + 1], M[off + 2], M[off + 3]);
+    else
+      return make_double2(M[off], M[off + 1]);
+  } else {
+    return *reinterpret_cast<const typename Vec16<T>::type*>(M + off);
+  }
+}
+
 // Even-odd line transforms (Kronbichler-style symmetry of a 1D eigenbasis).
 // The rows of M are indexed by nodes paired by the patch reflection
 // i <-> NR-1-i (P pairs, plus a centre node P when CEN, NR = 2P+1); the
@@ -178,7 +215,7 @@ __device__ __forceinline__ double vget(const double2& w, int e) { return e == 0 
 // Forward: out_j = sum_i M[i][j] v_i over rows; backward: out_i = sum_j
 // M[i][j] v_j.  Each needs only the first P (+1) rows and half the products.
 // Outputs past the real extent are zero.
-template <int N, int NR, int P, bool CEN, int SIG, int HE, int HO, int R, typename T>
+template <int N, int NR, int P, bool CEN, int SIG, int HE, int HO, int R, typename T, bool SCAL = false>
 __device__ __forceinline__ void eo_fwd(const T* __restrict__ M, const T (&v)[R][N], T (&res)[R][N]) {
   using V = typename Vec16<T>::type;
   constexpr int VW = Vec16<T>::width;
@@ -196,10 +233,9 @@ __device__ __forceinline__ void eo_fwd(const T* __restrict__ M, const T (&v)[R][
       a[r] = SIG > 0 ? x + y : x - y;  // feeds the even columns
       b[r] = SIG > 0 ? x - y : x + y;  // feeds the odd columns
     }
-    const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
 #pragma unroll
     for (int q = 0; q < NVEC; ++q) {
-      const V w = row[q];
+      const V w = mat_vec<SCAL, T>(M, i * kRowStride + q * VW);
 #pragma unroll
       for (int e = 0; e < VW; ++e) {
         const int j = q * VW + e;
@@ -210,10 +246,9 @@ __device__ __forceinline__ void eo_fwd(const T* __restrict__ M, const T (&v)[R][
     }
   }
   if (CEN) {
-    const V* row = reinterpret_cast<const V*>(M + P * kRowStride);
 #pragma unroll
     for (int q = 0; q < (HE + VW - 1) / VW; ++q) {
-      const V w = row[q];
+      const V w = mat_vec<SCAL, T>(M, P * kRowStride + q * VW);
 #pragma unroll
       for (int e = 0; e < VW; ++e) {
         const int j = q * VW + e;
@@ -225,20 +260,19 @@ __device__ __forceinline__ void eo_fwd(const T* __restrict__ M, const T (&v)[R][
   }
 }
 
-template <int N, int NR, int P, bool CEN, int SIG, int HE, int HO, int R, typename T>
+template <int N, int NR, int P, bool CEN, int SIG, int HE, int HO, int R, typename T, bool SCAL = false>
 __device__ __forceinline__ void eo_bwd(const T* __restrict__ M, const T (&v)[R][N], T (&res)[R][N]) {
   using V = typename Vec16<T>::type;
   constexpr int VW = Vec16<T>::width;
   constexpr int NCOL = HE + HO, NVEC = (NCOL + VW - 1) / VW;
 #pragma unroll
   for (int i = 0; i < P + (CEN ? 1 : 0); ++i) {
-    const V* row = reinterpret_cast<const V*>(M + i * kRowStride);
     T E[R], O[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) E[r] = O[r] = T(0);
 #pragma unroll
     for (int q = 0; q < NVEC; ++q) {
-      const V w = row[q];
+      const V w = mat_vec<SCAL, T>(M, i * kRowStride + q * VW);
 #pragma unroll
       for (int e = 0; e < VW; ++e) {
         const int j = q * VW + e;
@@ -305,7 +339,7 @@ __device__ __forceinline__ double scale_div(double a, double b) { return a / b; 
 // R lines through one 1D transform: FWD out_j = sum_i M[i][j] v_i (S^T, (B S)^T),
 // otherwise out_i = sum_j M[i][j] v_j (S, B S).  VELM: velocity eigenvectors
 // (SC / SD[t]) or the divergence / mass factors in the eigenbasis (EC / FM[t]).
-template <int K, typename T, bool FWD, bool VELM, int R, bool EO_ALL>
+template <int K, typename T, bool FWD, bool VELM, int R, bool EO_ALL, bool SCAL = false>
 __device__ __forceinline__ void line_transform(const T* __restrict__ M, bool eo, bool along_c,
                                                const T (&v)[R][PatchCfg<K>::NPD], T (&res)[R][PatchCfg<K>::NPD]) {
   using C = PatchCfg<K>;
@@ -317,20 +351,20 @@ __device__ __forceinline__ void line_transform(const T* __restrict__ M, bool eo,
     if (along_c) {
       if (VELM) {
         if (FWD)
-          eo_fwd<N, NPC, K, true, 1, K + 1, K, R>(M, v, res);
+          eo_fwd<N, NPC, K, true, 1, K + 1, K, R, T, SCAL>(M, v, res);
         else
-          eo_bwd<N, NPC, K, true, 1, K + 1, K, R>(M, v, res);
+          eo_bwd<N, NPC, K, true, 1, K + 1, K, R, T, SCAL>(M, v, res);
       } else {
         if (FWD)
-          eo_fwd<N, N, K + 1, false, -1, K + 1, K, R>(M, v, res);
+          eo_fwd<N, N, K + 1, false, -1, K + 1, K, R, T, SCAL>(M, v, res);
         else
-          eo_bwd<N, N, K + 1, false, -1, K + 1, K, R>(M, v, res);
+          eo_bwd<N, N, K + 1, false, -1, K + 1, K, R, T, SCAL>(M, v, res);
       }
     } else {
       if (FWD)
-        eo_fwd<N, N, K + 1, false, 1, K + 1, K + 1, R>(M, v, res);
+        eo_fwd<N, N, K + 1, false, 1, K + 1, K + 1, R, T, SCAL>(M, v, res);
       else
-        eo_bwd<N, N, K + 1, false, 1, K + 1, K + 1, R>(M, v, res);
+        eo_bwd<N, N, K + 1, false, 1, K + 1, K + 1, R, T, SCAL>(M, v, res);
     }
   } else if (FWD) {
     // one vector load feeds VW outputs of R lines
@@ -383,6 +417,27 @@ __device__ __forceinline__ void line_transform(const T* __restrict__ M, bool eo,
   }
 }
 
+// The transform of a pass: in the FP32 interior-patch kernel (EO_ALL) from
+// the matrices passed by value (constant bank), with the warp-uniform choice
+// of matrix (continuous or discontinuous direction of the warp's component)
+// as a branch so that every read has a compile-time offset; else from the
+// shared tables.  FP32 smoothing at k = 3 measured 19 % faster that way (the
+// kernel is bound by the shared-memory pipe); the FP64 kernel, bound by the
+// FP64 pipe, measured 5 % slower and keeps the shared tables.
+template <int K, typename T, bool FWD, bool VELM, int R, bool EO_ALL>
+__device__ __forceinline__ void pass_transform(const T* __restrict__ M, const InteriorMats<K, T>* im, bool eo,
+                                               bool along_c, const T (&v)[R][PatchCfg<K>::NPD],
+                                               T (&res)[R][PatchCfg<K>::NPD]) {
+  if constexpr (EO_ALL && sizeof(T) == 4) {
+    if (along_c)
+      line_transform<K, T, FWD, VELM, R, true, true>(VELM ? im->SC : im->EC, true, true, v, res);
+    else
+      line_transform<K, T, FWD, VELM, R, true, true>(VELM ? im->SD : im->FM, true, false, v, res);
+  } else {
+    line_transform<K, T, FWD, VELM, R, EO_ALL>(M, eo, along_c, v, res);
+  }
+}
+
 // One pass: every line along direction d of the three component tensors.
 // Every tensor is handled as (2k+2)^3 in its padded box: the continuous
 // direction of a velocity component has 2k+1 nodes, the extra node holds zero
@@ -396,9 +451,10 @@ __device__ __forceinline__ void line_transform(const T* __restrict__ M, bool eo,
 template <int K, typename T, int MODE, int EPI, bool EO_ALL>
 __device__ __forceinline__ void patch_pass(const T* __restrict__ in, T* __restrict__ out, int d, bool in_shared,
                                            const T* __restrict__ Ft, T* __restrict__ out2,
-                                           const PatchTables<T>& tb, const PatchGeo& g) {
+                                           const PatchTables<T>& tb, const PatchGeo& g,
+                                           const InteriorMats<K, T>* im) {
   using C = PatchCfg<K>;
-  constexpr int N = C::NPD, LPC = C::LPC, TPC = C::TPC, R = C::R;
+  constexpr int N = C::NPD, LPC = C::LPC, TPC = PatchThreads<K, T>::TPC, R = PatchThreads<K, T>::R;
   constexpr bool VELM = (MODE == VEL_FWD || MODE == VEL_BWD);
   constexpr bool FWD = (MODE == VEL_FWD || MODE == BT || MODE == BTBF);
   const int c = threadIdx.x / TPC, u = threadIdx.x - c * TPC;
@@ -423,7 +479,7 @@ __device__ __forceinline__ void patch_pass(const T* __restrict__ in, T* __restri
 #pragma unroll
     for (int i = 0; i < N; ++i) v[r][i] = src[base[r] + i * sd];
   }
-  line_transform<K, T, FWD, VELM, R, EO_ALL>(M, eo, along_c, v, res);
+  pass_transform<K, T, FWD, VELM, R, EO_ALL>(M, im, eo, along_c, v, res);
   // eigenvalues of the two fixed directions, then of the pass direction
   T lam_fixed[R];
   const T* lam_d = along_c ? tb.LC : tb.LD[td];
@@ -440,7 +496,7 @@ __device__ __forceinline__ void patch_pass(const T* __restrict__ in, T* __restri
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r][j] = scale_div(tb.inv_nu, lam_fixed[r] + ld) * res[r][j];
     }
-    line_transform<K, T, false, false, R, EO_ALL>(M, eo, along_c, v, res);
+    pass_transform<K, T, false, false, R, EO_ALL>(M, im, eo, along_c, v, res);
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -546,7 +602,7 @@ template <int K, typename T>
 __device__ __forceinline__ void patch_residual(const PatchArgs<T>& A, const int* v, const CellTables<T>& ct, T* F,
                                                T* G, T* Wn, T* Pst) {
   using C = PatchCfg<K>;
-  constexpr int ND = K + 1, NC = K + 2, NPD = C::NPD, BX = C::BX, BOX = C::BOX, NT = C::NT;
+  constexpr int ND = K + 1, NC = K + 2, NPD = C::NPD, BX = C::BX, BOX = C::BOX, NT = PatchThreads<K, T>::NT;
   constexpr int WC = 2 * K + 3;  // window nodes along c: the patch's two cells
   constexpr int WD = 4 * ND;     // window nodes along d1, d2: patch cells and one halo cell per side
   constexpr int UL = 8;          // window loads a thread has in flight
@@ -689,13 +745,15 @@ __device__ __forceinline__ void patch_residual(const PatchArgs<T>& A, const int*
 // (mode 3): the patch residual is computed in the kernel from x_in and b
 // (patch_residual) and the scatter writes x_out = x_in + R_j^T (U, P).
 template <int K, typename T, bool EO_ALL, bool FUSED = false>
-__device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk) {
+__device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk,
+                                            const InteriorMats<K, T>* im = nullptr) {
   using C = PatchCfg<K>;
+  using PT = PatchThreads<K, T>;
   constexpr int BX = C::BX, BOX = C::BOX, NPD = C::NPD;
   __shared__ PatchTables<T> tb;
-  __shared__ T red[3 * C::NW];
+  __shared__ T red[3 * PT::NW];
   T* red_a = red;          // single sums
-  T* red_b = red + C::NW;  // the second single sum of the setup, the pair sums of the CG
+  T* red_b = red + PT::NW;  // the second single sum of the setup, the pair sums of the CG
   extern __shared__ __align__(16) unsigned char patch_smem[];
   T* Ft = reinterpret_cast<T*>(patch_smem);  // 3 boxes: S^T F, kept to the end
   T* Ba = Ft + 3 * BOX;                      // 3 boxes of work space
@@ -710,15 +768,15 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   constexpr int UG = 8;              // global loads a thread has in flight in gather and scatter
   {
     // tables: 16-byte copies, all issued before the first store
-    constexpr int NQ = (int)(sizeof(PatchTables<T>) / 16), UQ = (NQ + C::NT - 1) / C::NT;
+    constexpr int NQ = (int)(sizeof(PatchTables<T>) / 16), UQ = (NQ + PT::NT - 1) / PT::NT;
     const int4* src = reinterpret_cast<const int4*>(A.tab);
     int4 q[UQ];
 #pragma unroll
     for (int u = 0; u < UQ; ++u)
-      if (tid + u * C::NT < NQ) q[u] = src[tid + u * C::NT];
+      if (tid + u * PT::NT < NQ) q[u] = src[tid + u * PT::NT];
 #pragma unroll
     for (int u = 0; u < UQ; ++u)
-      if (tid + u * C::NT < NQ) reinterpret_cast<int4*>(&tb)[tid + u * C::NT] = q[u];
+      if (tid + u * PT::NT < NQ) reinterpret_cast<int4*>(&tb)[tid + u * PT::NT] = q[u];
   }
 
   int v[3];
@@ -742,27 +800,27 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   // SDc = S d per component for the pressure box Dd: (B S) Lam^{-1} (B S)^T d,
   // passes x, y, z then z, y, x; returns the three component boxes to sum
   auto schur_apply = [&]() -> T* {
-    patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Dd, Ba, 0, true, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
+    patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Dd, Ba, 0, true, nullptr, nullptr, tb, g, im);
+    patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g, im);
     if constexpr (kFuseZ<K>) {
-      patch_pass<K, T, BTBF, EPI_NONE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 0, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BTBF, EPI_NONE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g, im);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g, im);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 0, false, nullptr, nullptr, tb, g, im);
       return Ba;
     } else {
-      patch_pass<K, T, BT, EPI_SCALE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 2, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
-      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
+      patch_pass<K, T, BT, EPI_SCALE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g, im);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 2, false, nullptr, nullptr, tb, g, im);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g, im);
+      patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g, im);
       return Bb;
     }
   };
 
   if (A.mode == 2) {  // column blk of the Schur complement of a patch of types btype
-    for (int q = tid; q < C::NP; q += C::NT) Dd[(q % NPD) + BX * (q / NPD)] = (q == blk) ? T(1) : T(0);
+    for (int q = tid; q < C::NP; q += PT::NT) Dd[(q % NPD) + BX * (q / NPD)] = (q == blk) ? T(1) : T(0);
     __syncthreads();
     const T* SDc = schur_apply();
-    for (int q = tid; q < C::NP; q += C::NT) {
+    for (int q = tid; q < C::NP; q += PT::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
       A.cols[(int64_t)blk * C::NP + q] = (double)(SDc[o] + SDc[BOX + o] + SDc[2 * BOX + o]);
     }
@@ -779,16 +837,16 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
     constexpr bool IN_FT = NCT <= 3 * BOX;
     __shared__ T ct_static[IN_FT ? 1 : NCT];
     T* ctp = IN_FT ? Ft : ct_static;
-    for (int i = tid; i < NCT; i += C::NT) ctp[i] = reinterpret_cast<const T*>(A.ctab)[i];
+    for (int i = tid; i < NCT; i += PT::NT) ctp[i] = reinterpret_cast<const T*>(A.ctab)[i];
     __syncthreads();
     patch_residual<K, T>(A, v, *reinterpret_cast<const CellTables<T>*>(ctp), Ba, Pp, Bb, R);
   }
-  for (int j0 = tid; !FUSED && j0 < NL; j0 += C::NT * UG) {
+  for (int j0 = tid; !FUSED && j0 < NL; j0 += PT::NT * UG) {
     T val[UG];
     int dst[UG];
 #pragma unroll
     for (int u = 0; u < UG; ++u) {
-      const int j = j0 + u * C::NT;
+      const int j = j0 + u * PT::NT;
       dst[u] = -1;
       val[u] = T(0);
       if (j < NL) {
@@ -805,7 +863,7 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
     for (int u = 0; u < UG; ++u)
       if (dst[u] >= 0) Ba[dst[u]] = val[u];
   }
-  for (int i = tid; i < 3 * NPD * NPD; i += C::NT) {
+  for (int i = tid; i < 3 * NPD * NPD; i += PT::NT) {
     const int c = i / (NPD * NPD), a = i % NPD, b = (i / NPD) % NPD;
     const int ii[3] = {c == 0 ? C::NPC : a, c == 1 ? C::NPC : (c == 0 ? a : b), c == 2 ? C::NPC : b};
     Ba[c * BOX + ii[0] + BX * (ii[1] + NPD * ii[2])] = T(0);
@@ -813,24 +871,24 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   __syncthreads();
 
   // ---- Ft = S^T F; Bb = Lam^{-1} Ft / nu
-  patch_pass<K, T, VEL_FWD, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
-  patch_pass<K, T, VEL_FWD, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
-  patch_pass<K, T, VEL_FWD, EPI_FT_AND_SCALE, EO_ALL>(Ba, Ft, 2, false, nullptr, Bb, tb, g);
+  patch_pass<K, T, VEL_FWD, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g, im);
+  patch_pass<K, T, VEL_FWD, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g, im);
+  patch_pass<K, T, VEL_FWD, EPI_FT_AND_SCALE, EO_ALL>(Ba, Ft, 2, false, nullptr, Bb, tb, g, im);
   // ---- R = sum_c (B_c S_c) Bb_c - G (not needed when P comes from the GEMM)
   T s1 = T(0), s2 = T(0), mean = T(0), rr = T(0), rr0 = T(0);
   if (A.gemm_phase != 2) {
-    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 0, false, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
-    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g);
-    for (int q = tid; q < C::NP; q += C::NT) {
+    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 0, false, nullptr, nullptr, tb, g, im);
+    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g, im);
+    patch_pass<K, T, BF, EPI_NONE, EO_ALL>(Bb, Ba, 2, false, nullptr, nullptr, tb, g, im);
+    for (int q = tid; q < C::NP; q += PT::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
       const T r = (Ba[o] + Ba[BOX + o] + Ba[2 * BOX + o]) - Pp[o];
       R[o] = r;
       s1 += r;
     }
-    mean = block_sum<T, C::NW>(s1, red_a) / T(C::NP);
+    mean = block_sum<T, PT::NW>(s1, red_a) / T(C::NP);
     s2 = T(0);
-    for (int q = tid; q < C::NP; q += C::NT) {
+    for (int q = tid; q < C::NP; q += PT::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
       const T r = R[o] - mean;
       R[o] = r;
@@ -838,15 +896,15 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
       Pp[o] = T(0);
       s2 += r * r;
     }
-    rr = block_sum<T, C::NW>(s2, red_b);
+    rr = block_sum<T, PT::NW>(s2, red_b);
     rr0 = rr;
   }
   if (A.gemm_phase == 1) {  // R leaves for the colour's GEMM
-    for (int q = tid; q < C::NP; q += C::NT) A.rout[(int64_t)blk * C::NP + q] = R[(q % NPD) + BX * (q / NPD)];
+    for (int q = tid; q < C::NP; q += PT::NT) A.rout[(int64_t)blk * C::NP + q] = R[(q % NPD) + BX * (q / NPD)];
     return;
   }
   if (A.gemm_phase == 2) {  // P = M R from the colour's GEMM
-    for (int q = tid; q < C::NP; q += C::NT) Pp[(q % NPD) + BX * (q / NPD)] = A.pin[(int64_t)blk * C::NP + q];
+    for (int q = tid; q < C::NP; q += PT::NT) Pp[(q % NPD) + BX * (q / NPD)] = A.pin[(int64_t)blk * C::NP + q];
     __syncthreads();
   }
 
@@ -861,9 +919,9 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
     // (19 % faster at k = 3 in FP32), else one output per load: thread t
     // owns outputs VW s .. VW s + VW-1 for s = t, t + NT, ...
     using V = typename Vec16<T>::type;
-    constexpr int VW = (C::NP / Vec16<T>::width >= C::NT) ? Vec16<T>::width : 1;
+    constexpr int VW = (C::NP / Vec16<T>::width >= PT::NT) ? Vec16<T>::width : 1;
     constexpr int NPV = C::NP / VW;                  // (2k+2)^3 is a multiple of 8
-    constexpr int NO = (NPV + C::NT - 1) / C::NT;    // vectors per thread
+    constexpr int NO = (NPV + PT::NT - 1) / PT::NT;    // vectors per thread
     T acc[NO][VW];
 #pragma unroll
     for (int u = 0; u < NO; ++u)
@@ -874,19 +932,19 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
       const T* colp = Mdir + (int64_t)j * C::NP;  // column j, across the threads
 #pragma unroll
       for (int u = 0; u < NO; ++u) {
-        if (tid + u * C::NT >= NPV) continue;
+        if (tid + u * PT::NT >= NPV) continue;
         if constexpr (VW == Vec16<T>::width)
-          vec_fma(acc[u], reinterpret_cast<const V*>(colp)[tid + u * C::NT], rj);
+          vec_fma(acc[u], reinterpret_cast<const V*>(colp)[tid + u * PT::NT], rj);
         else
-          acc[u][0] = fma(colp[tid + u * C::NT], rj, acc[u][0]);
+          acc[u][0] = fma(colp[tid + u * PT::NT], rj, acc[u][0]);
       }
     }
 #pragma unroll
     for (int u = 0; u < NO; ++u)
 #pragma unroll
       for (int e = 0; e < VW; ++e) {
-        const int q = (tid + u * C::NT) * VW + e;
-        if (tid + u * C::NT < NPV) Pp[(q % NPD) + BX * (q / NPD)] = acc[u][e];
+        const int q = (tid + u * PT::NT) * VW + e;
+        if (tid + u * PT::NT < NPV) Pp[(q % NPD) + BX * (q / NPD)] = acc[u][e];
       }
     __syncthreads();
   }
@@ -895,18 +953,18 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
     if (!(rr > T(0))) break;
     T* SDc = schur_apply();
     T part = T(0);
-    for (int q = tid; q < C::NP; q += C::NT) {
+    for (int q = tid; q < C::NP; q += PT::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
       const T s = SDc[o] + SDc[BOX + o] + SDc[2 * BOX + o];
       SD[o] = s;
       part += Dd[o] * s;
     }
-    const T dSd = block_sum<T, C::NW>(part, red_a);
+    const T dSd = block_sum<T, PT::NW>(part, red_a);
     if (!(dSd > T(0))) break;
     const T alpha = rr / dSd;
     s1 = T(0);
     s2 = T(0);
-    for (int q = tid; q < C::NP; q += C::NT) {
+    for (int q = tid; q < C::NP; q += PT::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
       Pp[o] += alpha * Dd[o];
       const T r = R[o] - alpha * SD[o];
@@ -914,12 +972,12 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
       s1 += r;
       s2 += r * r;
     }
-    block_sum2<T, C::NW>(s1, s2, red_b);
+    block_sum2<T, PT::NW>(s1, s2, red_b);
     mean = s1 / T(C::NP);
     T rr_new = s2 - s1 * mean;  // sum (r - mean)^2
     if (rr_new < T(0)) rr_new = T(0);
     const T beta = rr_new / rr;
-    for (int q = tid; q < C::NP; q += C::NT) {
+    for (int q = tid; q < C::NP; q += PT::NT) {
       const int o = (q % NPD) + BX * (q / NPD);
       const T r = R[o] - mean;
       R[o] = r;
@@ -930,20 +988,20 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
   }
 
   // ---- U_c = S_c Lam_c^{-1} (Ft_c - (B_c S_c)^T P) / nu
-  patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Pp, Ba, 0, true, nullptr, nullptr, tb, g);
-  patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g);
-  patch_pass<K, T, BT, EPI_SUB_SCALE, EO_ALL>(Bb, Ba, 2, false, Ft, nullptr, tb, g);
-  patch_pass<K, T, VEL_BWD, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g);
-  patch_pass<K, T, VEL_BWD, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g);
-  patch_pass<K, T, VEL_BWD, EPI_NONE, EO_ALL>(Ba, Bb, 2, false, nullptr, nullptr, tb, g);
+  patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Pp, Ba, 0, true, nullptr, nullptr, tb, g, im);
+  patch_pass<K, T, BT, EPI_NONE, EO_ALL>(Ba, Bb, 1, false, nullptr, nullptr, tb, g, im);
+  patch_pass<K, T, BT, EPI_SUB_SCALE, EO_ALL>(Bb, Ba, 2, false, Ft, nullptr, tb, g, im);
+  patch_pass<K, T, VEL_BWD, EPI_NONE, EO_ALL>(Ba, Bb, 0, false, nullptr, nullptr, tb, g, im);
+  patch_pass<K, T, VEL_BWD, EPI_NONE, EO_ALL>(Bb, Ba, 1, false, nullptr, nullptr, tb, g, im);
+  patch_pass<K, T, VEL_BWD, EPI_NONE, EO_ALL>(Ba, Bb, 2, false, nullptr, nullptr, tb, g, im);
 
   // ---- scatter: x += (U, P); UG loads of x per thread in flight
-  for (int j0 = tid; j0 < NL; j0 += C::NT * UG) {
+  for (int j0 = tid; j0 < NL; j0 += PT::NT * UG) {
     T val[UG], old[UG];
     int64_t gi[UG];
 #pragma unroll
     for (int u = 0; u < UG; ++u) {
-      const int j = j0 + u * C::NT;
+      const int j = j0 + u * PT::NT;
       gi[u] = -1;
       val[u] = T(0);
       if (j < NL) {
@@ -970,23 +1028,24 @@ __device__ __forceinline__ void patch_solve(const PatchArgs<T>& A, const int blk
 }
 
 template <int K, typename T, bool FUSED = false>
-__global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patch_kernel(PatchArgs<T> A) {
+__global__ void __launch_bounds__(PatchThreads<K, T>::NT, (PatchOcc<K, T>::value)) patch_kernel(PatchArgs<T> A) {
   patch_solve<K, T, false, FUSED>(A, blockIdx.x);
 }
 
 // Interior patches only: every 1D eigenbasis is symmetric, so the dense
 // transform code is not compiled in and the kernel's loop stays small in the
-// instruction cache.
+// instruction cache; the transform matrices come with the launch (IM).
 template <int K, typename T, bool FUSED = false>
-__global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value)) patch_kernel_interior(PatchArgs<T> A) {
-  patch_solve<K, T, true, FUSED>(A, blockIdx.x);
+__global__ void __launch_bounds__(PatchThreads<K, T>::NT, (PatchOcc<K, T>::value))
+    patch_kernel_interior(PatchArgs<T> A, InteriorMats<K, T> IM) {
+  patch_solve<K, T, true, FUSED>(A, blockIdx.x, &IM);
 }
 
 // One colour of several problems of the same degree in one launch: CTA b
 // solves patch b - first[j] of problem j (first[] ascending); the per-problem
 // fields replace those of the common arguments.
 template <int K, typename T>
-__global__ void __launch_bounds__(PatchCfg<K>::NT, (PatchOcc<K, T>::value))
+__global__ void __launch_bounds__(PatchThreads<K, T>::NT, (PatchOcc<K, T>::value))
     patch_kernel_multi(PatchArgs<T> A, PatchJobs<T> J) {
   int lo = 0, hi = J.count - 1;  // last job with first[job] <= blockIdx.x
   while (lo < hi) {

@@ -81,6 +81,10 @@ static void fill_common(const stk_problem* P, const Level& L, PatchArgs<T>& a) {
   a.gemm_phase = 0;
   a.rout = nullptr;
   a.pin = nullptr;
+  if constexpr (sizeof(T) == 8)
+    a.htab = &L.hptab64;
+  else
+    a.htab = &L.hptab32;
   for (int d = 0; d < 3; ++d) a.tlo[d] = a.cint[d] = a.btype[d] = 0;
 }
 
