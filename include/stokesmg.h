@@ -343,7 +343,10 @@ int stk_solve_batch(stk_problem* const* problems, int count, const double* const
  * halving down to 2) on the problem's stream and keep the
  * fastest, then, on every level that is smoothed, one smoothing step in each
  * form (fused_smoother 0 and 1, with the problem's local solver) and keep
- * the faster; every later apply, residual, smoothing step and solve of that
+ * the faster, then, in that form, one step with the interior patches of a
+ * colour in their own launch and one without, and keep the faster (levels
+ * whose interior eigenbases are symmetric); every later apply, residual,
+ * smoothing step and solve of that
  * dtype uses them (a V-cycle graph that an earlier solve captured in that
  * dtype is discarded, so the next solve captures the tuned launches).
  * Synchronous; allocates and frees two vectors per level (and builds the
@@ -354,6 +357,11 @@ int stk_autotune(stk_problem* P, int dtype);
  * 1 fused, -1 not tuned (stk_options.fused_smoother applies); no counterpart
  * in the paper. */
 int stk_tuned_smoother(const stk_problem* P, int level, int dtype, int* fused);
+
+/* Whether stk_autotune put the interior patches of a colour in their own
+ * launch on a level and dtype: 1 yes, 0 no, -1 not tuned (the built-in rule:
+ * from 8192 interior patches per colour); no counterpart in the paper. */
+int stk_tuned_split(const stk_problem* P, int level, int dtype, int* split);
 
 /* The run length chosen by stk_autotune (or set by stk_set_tuning) for a
  * level and dtype (0 = not tuned: the built-in choice is used, whole columns

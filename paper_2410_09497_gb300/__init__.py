@@ -98,6 +98,7 @@ def load_library():
         "stk_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "stk_set_tuning": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "stk_tuned_smoother": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "stk_tuned_split": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "stk_solve_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_double, ctypes.POINTER(SolveInfo)]),
         "stk_smooth_batch": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P)]),
         "stk_patch_eigen": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -315,16 +316,18 @@ class StokesMG:
         return x
 
     def autotune(self, dtype: int = F32, with_smoother: bool = False):
-        """Time the apply's march run length per level (and the smoother's form on
-        the smoothed levels) for dtype and keep the fastest; returns
-        {level: cells_per_run} or, with with_smoother, {level: (cells_per_run, fused)}."""
+        """Time the apply's march run length per level (and the smoother's form and
+        interior-patch launch split on the smoothed levels) for dtype and keep the
+        fastest; returns {level: cells_per_run} or, with with_smoother,
+        {level: (cells_per_run, fused, split)}."""
         self._check(self.lib.stk_autotune(self.h, int(dtype)))
         out = {}
         for level in range(self.num_levels):
-            v, f = ctypes.c_int(), ctypes.c_int()
+            v, f, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
             self._check(self.lib.stk_tuning(self.h, level, int(dtype), ctypes.byref(v)))
             self._check(self.lib.stk_tuned_smoother(self.h, level, int(dtype), ctypes.byref(f)))
-            out[level] = (v.value, f.value) if with_smoother else v.value
+            self._check(self.lib.stk_tuned_split(self.h, level, int(dtype), ctypes.byref(sp)))
+            out[level] = (v.value, f.value, sp.value) if with_smoother else v.value
         return out
 
     def set_tuning(self, level: int, dtype: int, cells_per_run: int):

@@ -629,6 +629,18 @@ int stk_autotune(stk_problem* P, int dtype) {
         if (e == cudaSuccess) e = cudaEventElapsedTime(&tf[form], e0, e1);
       }
       L.fused_pick[dtype] = tf[1] < tf[0] ? 1 : 0;
+      // then, in that form, the interior patches in their own launch or not
+      float ts[2] = {1e30f, 1e30f};
+      for (int sp = 0; sp < 2 && e == cudaSuccess && L.eo_interior; ++sp) {
+        L.split_pick[dtype] = sp;
+        e = stk::run_smooth(P, (int)l, dtype, x, y);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = stk::run_smooth(P, (int)l, dtype, x, y);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ts[sp], e0, e1);
+      }
+      if (L.eo_interior) L.split_pick[dtype] = ts[1] < ts[0] ? 1 : 0;
     }
     if (x) cudaFree(x);
     if (y) cudaFree(y);
@@ -643,6 +655,13 @@ int stk_tuned_smoother(const stk_problem* P, int level, int dtype, int* fused) {
   if (!P || !fused || level < 0 || level >= (int)P->levels.size() || (dtype != STK_F64 && dtype != STK_F32))
     return STK_EINVAL;
   *fused = P->levels[level].fused_pick[dtype];
+  return STK_OK;
+}
+
+int stk_tuned_split(const stk_problem* P, int level, int dtype, int* split) {
+  if (!P || !split || level < 0 || level >= (int)P->levels.size() || (dtype != STK_F64 && dtype != STK_F32))
+    return STK_EINVAL;
+  *split = P->levels[level].split_pick[dtype];
   return STK_OK;
 }
 

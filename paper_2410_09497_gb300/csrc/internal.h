@@ -184,6 +184,7 @@ struct Level {
   ContractTables<float> hce32{};
   int apply_chunk[2] = {0, 0};          // cells per run of the apply's velocity march ([dtype]); 0 = default
   int fused_pick[2] = {-1, -1};         // smoother form chosen by stk_autotune ([dtype]); -1 = the option's
+  int split_pick[2] = {-1, -1};         // interior patches in their own launch, chosen by stk_autotune ([dtype]); -1 = by count
   PatchTables<double>* ptab64 = nullptr;  // device
   PatchTables<float>* ptab32 = nullptr;   // device
   PatchTables<double> hptab64;            // host copies (the interior kernel's matrices go by value)

@@ -211,7 +211,10 @@ static cudaError_t patch_colour(const stk_problem* P, const Level& L, const Patc
   // Interior patches in their own launch (no dense transforms compiled in),
   // then the rest: 3-9 % faster per smoothing step at 64^3 (k = 2..4); at
   // 32^3 and below the second launch and its serialized tail cost as much.
-  if (!L.eo_interior || ni < kSplitInterior) return dispatch_patch<T>(P->k, a, nb, P->stream);
+  // stk_autotune may have timed both per level.
+  const int pick = L.split_pick[sizeof(T) == 8 ? STK_F64 : STK_F32];
+  const bool split = L.eo_interior && ni > 0 && (pick >= 0 ? pick == 1 : ni >= kSplitInterior);
+  if (!split) return dispatch_patch<T>(P->k, a, nb, P->stream);
   a.part = 1;
   cudaError_t e = dispatch_patch<T>(P->k, a, ni, P->stream);
   if (e != cudaSuccess || ni == nb) return e;

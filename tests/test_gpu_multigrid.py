@@ -319,8 +319,8 @@ def test_direct_local_solver_solve(stk):
 
 def test_autotuned_smoother_keeps_parity(stk):
     """stk_autotune also picks the smoother's form per smoothed level (split or
-    fused, the faster); the smoothing step it then runs still matches the
-    oracle's."""
+    fused, the faster) and whether the interior patches get their own launch;
+    the smoothing step it then runs still matches the oracle's."""
     n, k = 8, 2
     H = Hierarchy(n, k, local=("schur", 15))
     d = H.levels[-1].disc
@@ -330,6 +330,7 @@ def test_autotuned_smoother_keeps_parity(stk):
     P = stk.StokesMG(n, k, local_cg_mode=stk.CG_FIXED, local_cg_iters=15)
     tuned = P.autotune(stk.F64, with_smoother=True)
     assert tuned[0][1] == -1 and all(tuned[level][1] in (0, 1) for level in range(1, P.num_levels))
+    assert tuned[0][2] == -1 and all(tuned[level][2] in (0, 1) for level in range(1, P.num_levels))
     x = dev(x0.copy())
     P.smooth(x, dev(b))
     check(relerr(x.cpu().numpy(), ref), 1e-12)
