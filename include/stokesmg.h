@@ -360,7 +360,8 @@ int stk_tuned_smoother(const stk_problem* P, int level, int dtype, int* fused);
 
 /* Whether stk_autotune put the interior patches of a colour in their own
  * launch on a level and dtype: 1 yes, 0 no, -1 not tuned (the built-in rule:
- * from 8192 interior patches per colour); no counterpart in the paper. */
+ * from 8192 interior patches per colour in FP64, 1024 in FP32);
+ * no counterpart in the paper. */
 int stk_tuned_split(const stk_problem* P, int level, int dtype, int* split);
 
 /* The run length chosen by stk_autotune (or set by stk_set_tuning) for a

@@ -127,6 +127,7 @@ static cudaError_t direct_gemm(const stk_problem* P, const Level& L, int ni) {
 }
 
 constexpr int kSplitInterior = 8192;  // interior patches per colour from which they get their own launch
+constexpr int kSplitInteriorF32 = 1024;  // FP32, whose interior kernel reads its matrices from the constant bank
 
 // The interior patches of a colour (2 <= v <= n-2 in every direction) form a
 // box of the colour's patch grid: t in [tlo, tlo + cint) per direction.
@@ -210,10 +211,13 @@ static cudaError_t patch_colour(const stk_problem* P, const Level& L, const Patc
   }
   // Interior patches in their own launch (no dense transforms compiled in),
   // then the rest: 3-9 % faster per smoothing step at 64^3 (k = 2..4); at
-  // 32^3 and below the second launch and its serialized tail cost as much.
-  // stk_autotune may have timed both per level.
+  // 32^3 and below the second launch and its serialized tail cost as much,
+  // except in FP32, whose interior kernel is ~20 % faster than the general
+  // one (6 % faster smoothing at 32^3, k = 3).  stk_autotune may have timed
+  // both per level.
   const int pick = L.split_pick[sizeof(T) == 8 ? STK_F64 : STK_F32];
-  const bool split = L.eo_interior && ni > 0 && (pick >= 0 ? pick == 1 : ni >= kSplitInterior);
+  const int thr = sizeof(T) == 4 ? kSplitInteriorF32 : kSplitInterior;
+  const bool split = L.eo_interior && ni > 0 && (pick >= 0 ? pick == 1 : ni >= thr);
   if (!split) return dispatch_patch<T>(P->k, a, nb, P->stream);
   a.part = 1;
   cudaError_t e = dispatch_patch<T>(P->k, a, ni, P->stream);
