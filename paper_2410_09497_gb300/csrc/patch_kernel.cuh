@@ -68,7 +68,8 @@ struct PatchThreads {
 template <int K, typename T>
 struct InteriorMats {
   static constexpr int NPD = 2 * K + 2;
-  T SC[NPD * kRowStride], SD[NPD * kRowStride], EC[NPD * kRowStride], FM[NPD * kRowStride];
+  static constexpr int NE = sizeof(T) == 4 ? NPD * kRowStride : 1;  // FP64 reads its shared tables
+  T SC[NE], SD[NE], EC[NE], FM[NE];
 };
 
 // Resident CTAs per SM the register budget must allow: as many as the shared

@@ -25,13 +25,15 @@ cudaError_t launch_patch_k(PatchArgs<T> a, int nblocks, cudaStream_t s) {
   if (nblocks > 0) {
     const bool interior = (a.mode == 0 || fused) && a.part == 1;
     InteriorMats<K, T> im{};  // read by the FP32 interior kernel only
-    if (interior && sizeof(T) == 4) {
-      if (!a.htab) return cudaErrorInvalidValue;
-      constexpr int NE = InteriorMats<K, T>::NPD * kRowStride;
-      std::copy(a.htab->SC, a.htab->SC + NE, im.SC);
-      std::copy(a.htab->SD[0], a.htab->SD[0] + NE, im.SD);
-      std::copy(a.htab->EC, a.htab->EC + NE, im.EC);
-      std::copy(a.htab->FM[0], a.htab->FM[0] + NE, im.FM);
+    if constexpr (sizeof(T) == 4) {
+      if (interior) {
+        if (!a.htab) return cudaErrorInvalidValue;
+        constexpr int NE = InteriorMats<K, T>::NE;
+        std::copy(a.htab->SC, a.htab->SC + NE, im.SC);
+        std::copy(a.htab->SD[0], a.htab->SD[0] + NE, im.SD);
+        std::copy(a.htab->EC, a.htab->EC + NE, im.EC);
+        std::copy(a.htab->FM[0], a.htab->FM[0] + NE, im.FM);
+      }
     }
     if (fused) {
       if (interior)
