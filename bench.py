@@ -65,9 +65,9 @@ def velocity_flops_per_dof(k: int) -> float:
     return 2.0 * per_cell / nd
 
 
-def velocity_flops_survey(k: int) -> float:
-    """The scope table's algorithmic count: about 8k+14 multiply-adds per
-    velocity DoF (block-tridiagonal 1D penalty operators in the two
+def velocity_flops_banded(k: int) -> float:
+    """The hot path's reference algorithmic count: about 8k+14 multiply-adds
+    per velocity DoF (block-tridiagonal 1D penalty operators in the two
     discontinuous directions, a banded continuous direction, B^T p)."""
     return 2.0 * (8 * k + 14)
 
@@ -777,7 +777,7 @@ def run_ours(args):
     e2e = whole_job_rate(N, ws, K, t_e2e) / 1e9
     peaks, peak_src = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    vflops = velocity_flops_survey(k) * 3 * nv
+    vflops = velocity_flops_banded(k) * 3 * nv
     alu_peak = FP64_PEAK_TFLOPS if dt == torch.float64 else FP32_PEAK_TFLOPS
     achieved_tf = vflops / t_vel / 1e12
     traffic = DRAM_TRAFFIC.get((k, n, args.dtype))
@@ -793,7 +793,7 @@ def run_ours(args):
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak, "traffic": traffic,
                      "peak_source": "derived: 152 SMs x %s FMA/clk x 2 x 2.07 GHz" % ("2 FP64" if esize == 8 else "128 FP32"),
                      "ms_per_launch": t_vel * 1e3, "flop_per_launch": vflops,
-                     "flop_per_velocity_dof": velocity_flops_survey(k), "count": "8k+14 multiply-adds per velocity DoF",
+                     "flop_per_velocity_dof": velocity_flops_banded(k), "count": "8k+14 multiply-adds per velocity DoF",
                      "frac_at_dense_count": velocity_flops_per_dof(k) * 3 * nv / t_vel / 1e12 / alu_peak,
                      "frac_at_kernel_count": velocity_flops_kernel(k) * 3 * nv / t_vel / 1e12 / alu_peak},
         "hbm_roofline": {"achieved_gbs": apply_bytes * K / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
