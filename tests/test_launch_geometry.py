@@ -4,7 +4,8 @@ compute-sanitizer is not available to these tests, so the index arithmetic of
 the two largest kernels is restated here and checked against the buffers it
 addresses and against the oracle's own numbering:
 
-* patch smoother (Algorithm 2): which patch a CTA takes in each of the three
+* patch smoother (Algorithm 2): which lines each thread of a pass transforms,
+  which patch a CTA takes in each of the three
   launch kinds (every patch / interior patches / boundary patches), and the
   global DoF of every patch-local unknown.  The restated map must give the
   oracle's patch DoF set R_j in the same order, stay inside the vector, touch
@@ -120,6 +121,41 @@ def test_patch_index_map_equals_the_oracle_patch_sets(n, k):
             assert free[g].all()
             seen[g] += 1
         assert seen.max() <= 1, f"patches of colour {colour} share a DoF"
+
+
+# Restated from PatchThreads and patch_pass (patch_kernel.cuh): W warps per
+# velocity component (FP32: 1 for k <= 2, 2 for k = 3, 4, 3 for k = 5; FP64:
+# 1 for k <= 3, 2 for k = 4, 3 for k = 5), thread u of component c
+# transforms lines u, u + TPC, ... of the (2k+2)^2 lines of a pass.
+
+
+def patch_threads(k, f32):
+    w = ((1 if k <= 2 else (2 if k <= 4 else 3)) if f32 else (1 if k <= 3 else (2 if k == 4 else 3)))
+    tpc = 32 * w
+    lpc = (2 * k + 2) ** 2
+    r = (lpc + tpc - 1) // tpc
+    return w, tpc, r, 3 * tpc
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("f32", [True, False])
+def test_patch_pass_covers_every_line_once(k, f32):
+    w, tpc, r, nt = patch_threads(k, f32)
+    npd = 2 * k + 2
+    lpc = npd * npd
+    assert nt % 32 == 0 and nt <= 1024
+    for c in range(3):
+        seen = np.zeros(lpc, dtype=np.int32)
+        for tid in range(c * tpc, (c + 1) * tpc):
+            cc, u = tid // tpc, tid - (tid // tpc) * tpc
+            assert cc == c  # the component is warp-uniform: tpc is a multiple of 32
+            for rr in range(r):
+                line = u + rr * tpc
+                if line < lpc:
+                    seen[line] += 1
+        assert (seen == 1).all()
+    # the CTA-wide reductions use one partial per warp
+    assert nt // 32 == 3 * w
 
 
 # ---------------------------------------------------------------- apply kernel
